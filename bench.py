@@ -1,0 +1,381 @@
+#!/usr/bin/env python
+"""Benchmark of the coherent template-bank binary-pulsar search hot path.
+
+One step = one search request: every orbital template of the bank through
+index map -> gather -> FFT -> power -> de-reddening -> harmonic sum ->
+threshold -> compaction, over one synthetic series already resident in HBM.
+Default workload: HTRU-like circular search, 2^23 samples at 64 us, 4096
+templates, 16 harmonics, 6 sigma (synthetic noise + 3 injected pulsars).
+
+Prints ONE JSON line (rank 0).  ``--impl reference`` times the FP64 CPU oracle
+instead (the program the GPU results are checked against).
+"""
+from __future__ import annotations
+
+import argparse
+import hashlib
+import json
+import math
+import os
+import statistics
+import subprocess
+import sys
+import threading
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+import numpy as np  # noqa: E402
+
+import synth  # noqa: E402
+
+HBM_FALLBACK_GBS = 6400.0
+METRIC = "templates searched/sec at 2^23 samples vs plain GPU form; p50/p99 request latency"
+UNIT = "templates/s"
+# Algorithmic bytes per template per stage, in units of N (FP32 series):
+#   pass1: series read 4N + packed-complex write 4N; pass2: 4N read + 2N power write;
+#   median: 2N read; harmsum: 2N read.  Whole path (one series read, whitened
+#   spectrum written once and read once): 8N.
+STAGE_BYTES_PER_N = {"pass1": 8.0, "pass2": 6.0, "median": 2.0, "harmsum": 2.0,
+                     "power": 4.0 + 2.0, "anchors": 0.0}
+PATH_BYTES_PER_N = 8.0
+
+
+def parse():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=5)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--logn", type=int, default=23)
+    ap.add_argument("--templates", type=int, default=4096)
+    ap.add_argument("--batch", type=int, default=0)
+    ap.add_argument("--no-plain", action="store_true")
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--cpu-templates", type=int, default=0)
+    ap.add_argument("--cpu-threads", type=int, default=0)
+    return ap.parse_args()
+
+
+def peaks():
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
+            d = json.load(f)
+        return float(d["hbm_gbs"]), "measured"
+    except Exception:
+        return HBM_FALLBACK_GBS, "fallback"
+
+
+def kernel_source_hash():
+    h = hashlib.sha256()
+    for f in sorted(os.listdir(os.path.join(ROOT, "paper_2112_11991_b300", "csrc"))):
+        with open(os.path.join(ROOT, "paper_2112_11991_b300", "csrc", f), "rb") as fh:
+            h.update(fh.read())
+    return h.hexdigest()[:16]
+
+
+def ncu_traffic(stage, workload):
+    """DRAM bytes per launch of `stage` from the committed ncu summary, or None when
+    absent or taken on different kernel sources."""
+    try:
+        with open(os.path.join(ROOT, "profiles", "traffic.json")) as f:
+            d = json.load(f)
+        e = d[workload][stage]
+        if e.get("source_hash") != kernel_source_hash():
+            return None
+        return float(e["dram_bytes_per_launch"])
+    except Exception:
+        return None
+
+
+class ClockSampler:
+    """nvidia-smi clocks / throttle reasons sampled every 200 ms during the timed region."""
+    Q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+         "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+         "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu_id):
+        self.gpu_id = gpu_id
+        self.proc = None
+        self.lines = []
+
+    def start(self):
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", "--query-gpu=" + self.Q, "--format=csv,noheader,nounits",
+                 "-lms", "200", "-i", str(self.gpu_id)],
+                stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+            self.t = threading.Thread(target=self._read, daemon=True)
+            self.t.start()
+        except Exception:
+            self.proc = None
+
+    def _read(self):
+        for line in self.proc.stdout:
+            self.lines.append(line.strip())
+
+    def stop(self):
+        if not self.proc:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        time.sleep(0.25)
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except Exception:
+            self.proc.kill()
+        sm, mx, reasons, pw = [], [], set(), []
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for ln in self.lines:
+            f = [x.strip() for x in ln.split(",")]
+            if len(f) < 9:
+                continue
+            try:
+                sm.append(float(f[1]))
+                mx.append(float(f[2]))
+                pw.append(float(f[3]))
+            except ValueError:
+                continue
+            for nm, v in zip(names, f[5:9]):
+                if v.lower().startswith("active"):
+                    reasons.add(nm)
+        return {"sm_mhz": statistics.median(sm) if sm else None,
+                "sm_max_mhz": max(mx) if mx else None,
+                "power_w_max": max(pw) if pw else None,
+                "samples": len(sm), "reasons": sorted(reasons)}
+
+
+def dist_init(args):
+    ws = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    if ws > 1:
+        import torch.distributed as dist
+        os.environ.setdefault("MASTER_ADDR", "127.0.0.1")
+        dist.init_process_group("gloo", rank=rank, world_size=ws)
+    return ws, rank, local
+
+
+def barrier(ws):
+    if ws > 1:
+        import torch.distributed as dist
+        dist.barrier()
+
+
+def allmax(ws, v):
+    if ws == 1:
+        return v
+    import torch
+    import torch.distributed as dist
+    t = torch.tensor([v], dtype=torch.float64)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def workload(args, ws, rank):
+    n = 1 << args.logn
+    K = args.templates
+    w = synth.htru_circular(n=n, K=K * ws, seed=2)
+    bank = w.bank[rank * K:(rank + 1) * K]
+    return w, bank
+
+
+def oracle_rate(x, tsamp, bank, threads):
+    import oracle
+    t0 = time.perf_counter()
+    oracle.search(x, tsamp, bank, nthreads=threads, cap_per=1 << 15)
+    dt = time.perf_counter() - t0
+    return bank.shape[0] / dt, dt
+
+
+def cpu_threads(args):
+    c = os.cpu_count() or 1
+    return args.cpu_threads or max(1, min(c, 32))
+
+
+def run_reference(args, ws, rank):
+    """FP64 CPU oracle on the host cores, each step a bounded sample of the workload."""
+    if rank != 0:
+        return
+    w, bank = workload(args, 1, 0)
+    thr = cpu_threads(args)
+    per_step = args.cpu_templates or thr
+    sel = np.linspace(0, bank.shape[0] - 1, per_step * (args.steps + 1)).astype(int)
+    for i in range(args.warmup):
+        oracle_rate(w.series, w.tsamp, bank[sel[i:i + 1]], 1)
+    times = []
+    for s in range(args.steps):
+        b = bank[sel[s * per_step:(s + 1) * per_step]]
+        _, dt = oracle_rate(w.series, w.tsamp, b, thr)
+        times.append(dt)
+    value = per_step * args.steps / sum(times)
+    sample = "%d of %d templates per step (%d steps), 2^%d samples" % (
+        per_step, bank.shape[0], args.steps, args.logn)
+    out = {"impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": 0,
+           "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * statistics.mean(times),
+           "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+           "data": "synthetic", "config": config_of(w, args, ws),
+           "cpu_baseline": {"value": value, "unit": UNIT, "cores": thr, "kind": "oracle",
+                            "sample": sample},
+           "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(out), flush=True)
+
+
+def config_of(w, args, ws):
+    return {"workload": "HTRU-like circular search: 2^%d samples @ 64 us, %d circular templates "
+                        "(Porb U[3T,10T], tau U[0,3] lt-s), 16 harmonics, 6 sigma, "
+                        "3 injected P-BH pulsars" % (args.logn, args.templates),
+            "n_samples": 1 << args.logn, "tsamp_s": w.tsamp, "templates_per_gpu": args.templates,
+            "global_templates": args.templates * ws, "nharm_max": 16, "whiten_block": 1024,
+            "sigma": 6.0, "parallelism": "template shards, replicas" if ws > 1 else "1 GPU",
+            "l2": "flushed between timed steps (256 MiB write)"}
+
+
+def main():
+    args = parse()
+    ws, rank, local = dist_init(args)
+    if args.impl == "reference":
+        run_reference(args, ws, rank)
+        return
+    import torch
+
+    import paper_2112_11991_b300 as bps
+    from paper_2112_11991_b300 import build
+    if rank == 0 or ws == 1:
+        build.build()
+    barrier(ws)
+    torch.cuda.set_device(local)
+    dev = torch.device("cuda", local)
+    w, bank = workload(args, ws, rank)
+    n = w.n
+    K = bank.shape[0]
+    ctx = bps.Context(local)
+    stream = torch.cuda.current_stream(dev)
+    sid = ctx.load_series(w.series, w.tsamp)
+    bid = ctx.load_bank(bank)
+    flush = torch.empty(256 << 20, dtype=torch.uint8, device=dev)
+
+    def timed_steps(mode, steps, warmup, profile):
+        prm = bps.default_params(mode=mode, batch=args.batch if mode == 0 else 0)
+        ctx.set_profiling(False)
+        for _ in range(warmup):
+            rid = ctx.search(sid, bid, prm, stream=stream)
+            ctx.fetch_candidates(rid, cap=0)
+            ctx.unload(rid)
+        ctx.set_profiling(profile)
+        ms, stats, ncand = [], [], 0
+        barrier(ws)
+        torch.cuda.synchronize(dev)
+        for _ in range(steps):
+            flush.zero_()
+            a = torch.cuda.Event(enable_timing=True)
+            b = torch.cuda.Event(enable_timing=True)
+            a.record(stream)
+            rid = ctx.search(sid, bid, prm, stream=stream)
+            b.record(stream)
+            b.synchronize()
+            ms.append(a.elapsed_time(b))
+            stats.append(ctx.request_stats(rid))
+            _, tot = ctx.fetch_candidates(rid, cap=0)
+            ncand = tot
+            ctx.unload(rid)
+        torch.cuda.synchronize(dev)
+        barrier(ws)
+        ctx.set_profiling(False)
+        return ms, stats, ncand
+
+    clocks = ClockSampler(local)
+    clocks.start()
+    ms, stats, ncand = timed_steps(0, args.steps, args.warmup, True)
+    clk = clocks.stop()
+    total_s = allmax(ws, sum(ms) / 1e3)
+    value = K * ws * args.steps / total_s
+
+    plain = None
+    if not args.no_plain:
+        pms, pstats, pc = timed_steps(1, max(2, min(args.steps, 3)), 1, False)
+        ptot = allmax(ws, sum(pms) / 1e3)
+        plain = {"value": K * ws * len(pms) / ptot, "unit": UNIT,
+                 "ms_per_step": statistics.mean(pms), "candidates": pc,
+                 "form": "index map + gather kernel -> cuFFT R2C -> power -> same median/harmonic-sum kernels, one template per launch"}
+
+    # end to end through the public API with host buffers: pinned series H2D, bank, search,
+    # candidate D2H, unload -- every step.
+    pinned = torch.from_numpy(w.series).pin_memory()
+    e2e_ms = []
+    d2h = 0
+    prm = bps.default_params(batch=args.batch)
+    for i in range(args.warmup + args.steps):
+        torch.cuda.synchronize(dev)
+        t0 = time.perf_counter()
+        s2 = ctx.load_series(pinned, w.tsamp)
+        b2 = ctx.load_bank(bank)
+        rid = ctx.search(s2, b2, prm, stream=stream)
+        c, tot = ctx.fetch_candidates(rid)
+        ctx.unload(rid)
+        ctx.unload(s2)
+        ctx.unload(b2)
+        t1 = time.perf_counter()
+        if i >= args.warmup:
+            e2e_ms.append(1e3 * (t1 - t0))
+            d2h = c.nbytes + 8
+    e2e_tot = allmax(ws, sum(e2e_ms) / 1e3)
+    e2e = {"value": K * ws * len(e2e_ms) / e2e_tot, "unit": UNIT,
+           "h2d_bytes_per_step": int(w.series.nbytes + bank.nbytes),
+           "d2h_bytes_per_step": int(d2h),
+           "ms_per_step": statistics.mean(e2e_ms),
+           "p50_ms": float(np.percentile(e2e_ms, 50)), "p99_ms": float(np.percentile(e2e_ms, 99))}
+
+    # roofline of the dominant kernel from the live stage events of the timed steps
+    peak, peak_kind = peaks()
+    stage_ms = {k: sum(s["stage_ms"][k] for s in stats) for k in bps.STAGES}
+    stage_launch = {k: sum(s["stage_launches"][k] for s in stats) for k in bps.STAGES}
+    dom = max(stage_ms, key=stage_ms.get)
+    batch = stats[0]["batch"]
+    per_launch_ms = stage_ms[dom] / max(1, stage_launch[dom])
+    alg_bytes = STAGE_BYTES_PER_N[dom] * n * batch
+    achieved = alg_bytes / (per_launch_ms * 1e-3) / 1e9
+    traffic = ncu_traffic(dom, "htru_2p%d" % args.logn)
+    roof = {"bound": "hbm", "kernel": dom, "achieved": achieved, "peak": peak, "unit": "GB/s",
+            "frac": achieved / peak, "peak_kind": peak_kind, "traffic": traffic,
+            "alg_bytes_per_launch": alg_bytes, "templates_per_launch": batch,
+            "ms_per_launch": per_launch_ms}
+    path_gbs = PATH_BYTES_PER_N * n * K * args.steps / (sum(ms) / 1e3) / 1e9
+    stage_share = {k: v / max(1e-9, sum(stage_ms.values())) for k, v in stage_ms.items()}
+
+    cpu = None
+    if rank == 0 and not args.no_cpu_baseline:
+        thr = cpu_threads(args)
+        nt = args.cpu_templates or thr
+        sel = np.linspace(0, K - 1, nt).astype(int)
+        rate, dt = oracle_rate(w.series, w.tsamp, bank[sel], thr)
+        cpu = {"value": rate, "unit": UNIT, "cores": thr, "kind": "oracle",
+               "sample": "%d of %d templates of the 2^%d-sample workload (%.1f s)" % (
+                   nt, K, args.logn, dt)}
+
+    launches = sum(s["launches"] for s in stats)
+    out = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": ws, "steps": args.steps,
+           "warmup": args.warmup, "ms_per_step": statistics.mean(ms), "higher_is_better": True,
+           "scaling": "weak", "vs_baseline": None, "dtype": "f32",
+           "data": "synthetic (seeded noise + injected pulsars)",
+           "config": config_of(w, args, ws),
+           "latency_ms": {"p50": float(np.percentile(ms, 50)), "p99": float(np.percentile(ms, 99))},
+           "plain_form": plain,
+           "speedup_vs_plain": (value / plain["value"]) if plain else None,
+           "roofline": roof,
+           "path_roofline": {"achieved": path_gbs, "peak": peak, "unit": "GB/s",
+                             "frac": path_gbs / peak, "alg_bytes_per_template": PATH_BYTES_PER_N * n},
+           "stage_ms_per_step": {k: v / args.steps for k, v in stage_ms.items()},
+           "stage_share": stage_share,
+           "cpu_baseline": cpu, "e2e": e2e, "clocks": clk, "gpu_launches": launches,
+           "candidates_per_step": ncand, "anchor_block": stats[0]["anchor_block"]}
+    if rank == 0:
+        print(json.dumps(out), flush=True)
+    ctx.close()
+    if ws > 1:
+        import torch.distributed as dist
+        dist.destroy_process_group()
+
+
+if __name__ == "__main__":
+    main()

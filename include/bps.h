@@ -1,0 +1,211 @@
+/*
+ * bps.h -- C ABI of the B300-native coherent template-bank binary-pulsar search
+ * (Balakrishnan et al., arXiv:2112.11991).
+ *
+ * The library runs, for every orbital template of a bank, the per-template hot
+ * path of the paper on one CUDA device (sm_103a):
+ *
+ *   index map (BT Roemer delay + Kepler, App. A, Algorithm 1)
+ *   -> nearest-neighbour resampling gather (Algorithm 1)
+ *   -> real FFT of the resampled series (Sec. 2.4: uniform f0 grid)
+ *   -> power |X_k|^2 (Sec. 2.1, detection statistic)
+ *   -> block-median de-reddening (App. A, "Fourier de-reddening")
+ *   -> incoherent 1/2/4/8/16-harmonic sums (Sec. 2.1, S_L)
+ *   -> threshold (Sec. 2.1, false-alarm statistics) and compaction.
+ *
+ * Conventions (readings of the paper, identical in the FP64 oracle):
+ *   off_j = (Delta_R(0) - Delta_R(j t_s)) / t_s,  idx_j = j + floor(off_j + 1/2),
+ *   resampled x'_j = x[idx_j] (series mean when idx_j is outside [0, n));
+ *   X_k = sum_j x'_j exp(-2 pi i j k / n), k in [0, n/2), P_0 := 0;
+ *   Pw_k = P_k ln2 / med_b, med_b the lower median of block b of W bins;
+ *   S_n[k] = sum_{h=1}^{n} Pw[(k h + n/2) div n], k in [1, n/2);
+ *   candidate (template, n, k) when S_n[k] >= thr_n, where thr_n solves
+ *   Q(n, thr_n) = erfc(sigma / sqrt 2) / 2 and Q is the Gamma(n, 1) tail.
+ *
+ * Errors: every int-returning call returns BPS_OK (0) or a negative BPS_ERR_*
+ * code; bps_last_error() then holds a message.  Calls on one context are
+ * serialised by an internal mutex (thread-safe per context).
+ * Ownership: the library copies series and banks into device memory it owns
+ * (or borrows a caller device pointer, see bps_load_series); output buffers
+ * passed to the library belong to the caller.  Host pointers must stay valid
+ * for the duration of the call only.
+ */
+#ifndef BPS_H
+#define BPS_H
+
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+/* ---- error codes ---------------------------------------------------------- */
+#define BPS_OK                  0
+#define BPS_ERR_INVALID_ARG    -1  /* bad size, parameter or id                   */
+#define BPS_ERR_OUT_OF_MEMORY  -2  /* device allocation refused (admission)       */
+#define BPS_ERR_NOT_READY      -3  /* request still running                       */
+#define BPS_ERR_CAND_OVERFLOW  -4  /* candidates truncated; n_total is the truth   */
+#define BPS_ERR_TIMEOUT        -5  /* a bounded wait expired                      */
+#define BPS_ERR_CUDA           -6  /* CUDA runtime / launch failure               */
+#define BPS_ERR_UNSUPPORTED    -7  /* size or mode outside what is built          */
+
+/* ---- series dtypes --------------------------------------------------------- */
+#define BPS_F32          0  /* float32 samples                                    */
+#define BPS_F16_SCALED   1  /* float32 input, stored on device as FP16 with one   */
+                            /* power-of-two FP32 scale per 4096 samples            */
+
+/* ---- search modes (bps_search_params.mode) ------------------------------- */
+#define BPS_MODE_FUSED   0  /* hand-written kernels: gather fused into FFT pass 1, */
+                            /* split + power fused into pass 2                     */
+#define BPS_MODE_PLAIN   1  /* plain FP32 per-template form: index map -> gather   */
+                            /* -> cuFFT R2C -> power; same whitening/harmonic sum  */
+
+/* One orbital template (App. A, BT model).  Circular templates: omega = ecc = 0,
+ * for which Delta_R = tau sin(Omega t + phi) (Sec. 2.1, circular phase model). */
+typedef struct {
+    double porb_s;    /* orbital period P_orb [s], > 0 ; Omega = 2 pi / P_orb    */
+    double tau_lts;   /* projected semi-major axis a sin(eps)/c [lt-s], >= 0     */
+    double phi_rad;   /* initial orbital phase alpha [rad] (M(0) = alpha)         */
+    double omega_rad; /* longitude of periastron psi [rad]                         */
+    double ecc;       /* eccentricity e in [0, 1)                                  */
+} bps_template;
+
+/* One detection: harmonic sum S_n[bin] >= thr_n.  The fundamental frequency is
+ * bin / (nharm * T), T = n_samples * t_samp.  16 bytes. */
+typedef struct {
+    uint32_t template_idx; /* index into the bank                                  */
+    uint16_t nharm;        /* n in {1, 2, 4, 8, 16}                                 */
+    uint16_t flags;        /* reserved, 0                                           */
+    uint32_t bin;          /* k, the bin of the n-th harmonic                       */
+    float    power;        /* S_n[k] in units of the whitened noise mean            */
+} bps_candidate;
+
+typedef struct {
+    int32_t nharm_max;     /* 1, 2, 4, 8 or 16 (Sec. 2.1: up to 16 harmonics)       */
+    int32_t whiten_block;  /* W: power of two in [32, n/2]; 1024 in the paper's runs */
+    double  sigma_thr;     /* Gaussian-equivalent significance of the threshold     */
+    int32_t auto_thr;      /* 1: sigma = S/N_min(n_trials), n_trials =              */
+                           /*    (n/2) * levels * templates (Sec. 2.1)               */
+    int32_t mode;          /* BPS_MODE_FUSED or BPS_MODE_PLAIN                      */
+    int64_t cand_cap;      /* device candidate capacity of the request (>= 1)       */
+    int32_t precision;     /* reserved, 0 (the storage precision is the series')    */
+    int32_t batch;         /* templates per launch batch; 0 = library's choice       */
+} bps_search_params;
+
+typedef struct bps_ctx bps_ctx;
+
+/* Fill *p with the defaults: nharm_max 16, W 1024, sigma 6, fused mode,
+ * cand_cap 1<<20, batch 0. */
+void bps_default_params(bps_search_params* p);
+
+/* Create a context bound to CUDA device `device`.  *out receives the handle.
+ * Returns BPS_ERR_CUDA if the device cannot be used. */
+int bps_create(bps_ctx** out, int device);
+
+/* Destroy a context: waits for its work, frees every series, bank and request. */
+void bps_destroy(bps_ctx* ctx);
+
+/* Load a dedispersed time series S sampled at t_samp (App. A.1: "dedispersed
+ * timeseries S ... sampled at t_samp").
+ *   data      n float32 samples (host pointer, or device pointer if on_device)
+ *   n         power of two in [2^11, 2^25]
+ *   tsamp_s   sampling time [s], > 0
+ *   dtype     BPS_F32 or BPS_F16_SCALED (storage on the device)
+ *   on_device 0: data is host memory, copied; 1: data is device memory of this
+ *             context's device -- copied for BPS_F16_SCALED, borrowed (not
+ *             copied, caller keeps it alive until bps_unload) for BPS_F32
+ * The series mean (the fill value for samples mapped outside the series) is
+ * computed on the device in FP64.  *series_id receives an id (> 0). */
+int bps_load_series(bps_ctx* ctx, const void* data, int64_t n, double tsamp_s,
+                    int dtype, int on_device, int64_t* series_id);
+
+/* Load a template bank (Algorithm 1: "K orbital templates in template bank").
+ * t: host array of count templates (copied).  Checks porb > 0, tau >= 0,
+ * 0 <= ecc < 1, finite values.  *bank_id receives an id (> 0). */
+int bps_load_bank(bps_ctx* ctx, const bps_template* t, int64_t count, int64_t* bank_id);
+
+/* Enqueue the search of every template of a bank over a series on
+ * `cuda_stream` (a cudaStream_t; NULL = the context's own stream).  Returns at
+ * once; *req_id receives a request id.  Workspace is allocated stream-ordered
+ * and freed when the request completes. */
+int bps_search(bps_ctx* ctx, int64_t series_id, int64_t bank_id,
+               const bps_search_params* params, void* cuda_stream, int64_t* req_id);
+
+/* Non-blocking completion test: *done = 1 when the request has finished. */
+int bps_query(bps_ctx* ctx, int64_t req_id, int* done);
+
+/* Wait for a request and copy its candidates, sorted by (template_idx, nharm,
+ * bin), into out[0 .. cap).  *n_written = candidates copied, *n_total = all
+ * candidates found.  Returns BPS_ERR_CAND_OVERFLOW when the device capacity
+ * (cand_cap) was exceeded: then the kept subset is arbitrary. */
+int bps_fetch_candidates(bps_ctx* ctx, int64_t req_id, bps_candidate* out,
+                         int64_t cap, int64_t* n_written, int64_t* n_total);
+
+/* Free a series, bank or request id. */
+int bps_unload(bps_ctx* ctx, int64_t id);
+
+/* Message of the last error on this context (never NULL). */
+const char* bps_last_error(bps_ctx* ctx);
+
+/* ---- stage entry points (inspection and parity; same kernels as bps_search) */
+
+/* Algorithm 1 index map of one template: idx_out[j] = idx_j for j in [0, n)
+ * (int32, host buffer of n entries).  *n_precise receives how many samples
+ * took the compensated-precision branch (offset within 1e-4 of a rounding
+ * boundary in the fast evaluation). */
+int bps_index_map(bps_ctx* ctx, int64_t series_id, int64_t bank_id,
+                  int64_t template_idx, int32_t* idx_out, int64_t* n_precise);
+
+/* Whitened power spectrum Pw_k, k in [0, n/2), of templates [t0, t0 + count)
+ * into pw_out (host, count * n/2 floats, template-major). */
+int bps_whitened_spectrum(bps_ctx* ctx, int64_t series_id, int64_t bank_id,
+                          int64_t t0, int64_t count, const bps_search_params* params,
+                          float* pw_out);
+
+/* Harmonic sums S_{2^L}[k] of one template, L in [0, levels), k in [0, n/2),
+ * into s_out (host, levels * n/2 floats, level-major; S[.][0] = 0). */
+int bps_harmonic_sums(bps_ctx* ctx, int64_t series_id, int64_t bank_id,
+                      int64_t template_idx, const bps_search_params* params,
+                      float* s_out);
+
+/* ---- measurement ------------------------------------------------------------ */
+
+/* Stage indices of bps_stats.stage_ms / stage_launches. */
+#define BPS_STAGE_ANCHORS   0  /* FP64 anchor kernel                               */
+#define BPS_STAGE_PASS1     1  /* fused: index map + gather + column FFTs          */
+                               /* plain: index map + gather into a series          */
+#define BPS_STAGE_PASS2     2  /* fused: row FFTs + real split + power; plain: cuFFT */
+#define BPS_STAGE_POWER     3  /* plain only: |X_k|^2                               */
+#define BPS_STAGE_MEDIAN    4  /* block lower medians                              */
+#define BPS_STAGE_HARMSUM   5  /* harmonic sums + threshold + compaction           */
+#define BPS_NSTAGES         6
+
+typedef struct {
+    int64_t templates;       /* templates searched                                 */
+    int32_t batch;           /* templates per launch                               */
+    int32_t anchor_block;    /* B, samples per FP64 anchor                          */
+    int32_t launches;        /* kernel launches of this library (cuFFT counted 1)   */
+    int32_t profiled;        /* 1 when stage_ms holds CUDA-event timings            */
+    int32_t stage_launches[8];
+    float   stage_ms[8];     /* summed device time per stage (profiled requests)    */
+} bps_stats;
+
+/* Enable (1) or disable (0) per-stage CUDA-event timing of later bps_search calls
+ * on this context.  Events are recorded on the request's stream around each
+ * stage launch. */
+int bps_set_profiling(bps_ctx* ctx, int on);
+
+/* Statistics of a finished request (waits for it).  Stage times are filled only
+ * when profiling was on when the request was enqueued. */
+int bps_request_stats(bps_ctx* ctx, int64_t req_id, bps_stats* out);
+
+/* Per-level thresholds thr_n (n = 1, 2, ..., nharm_max) the search will use for
+ * these parameters and problem size (host FP64). */
+int bps_thresholds(const bps_search_params* params, int64_t n_samples,
+                   int64_t n_templates, double* thr_out);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* BPS_H */

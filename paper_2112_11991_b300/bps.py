@@ -1,0 +1,361 @@
+"""ctypes binding of ``libbps.so`` (C ABI in include/bps.h).
+
+Argument marshalling only: every step of the search runs in the library's CUDA
+kernels.  There is no CPU fallback -- if the library is missing or no CUDA
+device is present the calls raise :class:`BpsError`.
+
+Functions keep the C names (``bps_create`` ...); :class:`Context` wraps them.
+Arrays may be numpy arrays (host) or torch tensors (host or CUDA; a CUDA float32
+tensor is passed by device pointer).
+"""
+from __future__ import annotations
+
+import ctypes as C
+import os
+
+import numpy as np
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+_LIB_PATH = os.path.join(_HERE, "libbps.so")
+_lib = None
+
+BPS_OK = 0
+BPS_ERR_INVALID_ARG = -1
+BPS_ERR_OUT_OF_MEMORY = -2
+BPS_ERR_NOT_READY = -3
+BPS_ERR_CAND_OVERFLOW = -4
+BPS_ERR_TIMEOUT = -5
+BPS_ERR_CUDA = -6
+BPS_ERR_UNSUPPORTED = -7
+
+BPS_F32 = 0
+BPS_F16_SCALED = 1
+BPS_MODE_FUSED = 0
+BPS_MODE_PLAIN = 1
+
+EXPORTED = ["bps_default_params", "bps_create", "bps_destroy", "bps_load_series",
+            "bps_load_bank", "bps_search", "bps_query", "bps_fetch_candidates",
+            "bps_unload", "bps_last_error", "bps_index_map", "bps_whitened_spectrum",
+            "bps_harmonic_sums", "bps_thresholds", "bps_set_profiling",
+            "bps_request_stats"]
+STAGES = ["anchors", "pass1", "pass2", "power", "median", "harmsum"]
+
+
+class BpsError(RuntimeError):
+    def __init__(self, code, msg):
+        super().__init__("bps error %d: %s" % (code, msg))
+        self.code = code
+
+
+class bps_template(C.Structure):
+    _fields_ = [("porb_s", C.c_double), ("tau_lts", C.c_double), ("phi_rad", C.c_double),
+                ("omega_rad", C.c_double), ("ecc", C.c_double)]
+
+
+class bps_candidate(C.Structure):
+    _fields_ = [("template_idx", C.c_uint32), ("nharm", C.c_uint16), ("flags", C.c_uint16),
+                ("bin", C.c_uint32), ("power", C.c_float)]
+
+
+class bps_search_params(C.Structure):
+    _fields_ = [("nharm_max", C.c_int32), ("whiten_block", C.c_int32), ("sigma_thr", C.c_double),
+                ("auto_thr", C.c_int32), ("mode", C.c_int32), ("cand_cap", C.c_int64),
+                ("precision", C.c_int32), ("batch", C.c_int32)]
+
+
+class bps_stats(C.Structure):
+    _fields_ = [("templates", C.c_int64), ("batch", C.c_int32), ("anchor_block", C.c_int32),
+                ("launches", C.c_int32), ("profiled", C.c_int32),
+                ("stage_launches", C.c_int32 * 8), ("stage_ms", C.c_float * 8)]
+
+
+CAND_DTYPE = np.dtype([("template_idx", np.uint32), ("nharm", np.uint16), ("flags", np.uint16),
+                       ("bin", np.uint32), ("power", np.float32)])
+
+
+def library_path() -> str:
+    return _LIB_PATH
+
+
+def lib():
+    """Load libbps.so (raises BpsError when it has not been built)."""
+    global _lib
+    if _lib is None:
+        if not os.path.exists(_LIB_PATH):
+            raise BpsError(BPS_ERR_UNSUPPORTED,
+                           "libbps.so not built (run paper_2112_11991_b300/build.py)")
+        L = C.CDLL(_LIB_PATH)
+        vp, i64, i32, P = C.c_void_p, C.c_int64, C.c_int, C.POINTER
+        L.bps_default_params.restype = None
+        L.bps_default_params.argtypes = [P(bps_search_params)]
+        L.bps_create.restype = i32
+        L.bps_create.argtypes = [P(vp), i32]
+        L.bps_destroy.restype = None
+        L.bps_destroy.argtypes = [vp]
+        L.bps_load_series.restype = i32
+        L.bps_load_series.argtypes = [vp, vp, i64, C.c_double, i32, i32, P(i64)]
+        L.bps_load_bank.restype = i32
+        L.bps_load_bank.argtypes = [vp, vp, i64, P(i64)]
+        L.bps_search.restype = i32
+        L.bps_search.argtypes = [vp, i64, i64, P(bps_search_params), vp, P(i64)]
+        L.bps_query.restype = i32
+        L.bps_query.argtypes = [vp, i64, P(i32)]
+        L.bps_fetch_candidates.restype = i32
+        L.bps_fetch_candidates.argtypes = [vp, i64, vp, i64, P(i64), P(i64)]
+        L.bps_unload.restype = i32
+        L.bps_unload.argtypes = [vp, i64]
+        L.bps_last_error.restype = C.c_char_p
+        L.bps_last_error.argtypes = [vp]
+        L.bps_index_map.restype = i32
+        L.bps_index_map.argtypes = [vp, i64, i64, i64, vp, P(i64)]
+        L.bps_whitened_spectrum.restype = i32
+        L.bps_whitened_spectrum.argtypes = [vp, i64, i64, i64, i64, P(bps_search_params), vp]
+        L.bps_harmonic_sums.restype = i32
+        L.bps_harmonic_sums.argtypes = [vp, i64, i64, i64, P(bps_search_params), vp]
+        L.bps_set_profiling.restype = i32
+        L.bps_set_profiling.argtypes = [vp, i32]
+        L.bps_request_stats.restype = i32
+        L.bps_request_stats.argtypes = [vp, i64, P(bps_stats)]
+        L.bps_thresholds.restype = i32
+        L.bps_thresholds.argtypes = [P(bps_search_params), i64, i64, vp]
+        _lib = L
+    return _lib
+
+
+def default_params(**kw) -> bps_search_params:
+    p = bps_search_params()
+    lib().bps_default_params(C.byref(p))
+    for k, v in kw.items():
+        if not hasattr(p, k):
+            raise TypeError("unknown search parameter %r" % k)
+        setattr(p, k, v)
+    return p
+
+
+def _np_ptr(a: np.ndarray):
+    return a.ctypes.data_as(C.c_void_p)
+
+
+def _stream_ptr(stream):
+    if stream is None:
+        return None
+    if isinstance(stream, int):
+        return C.c_void_p(stream)
+    return C.c_void_p(int(stream.cuda_stream))
+
+
+def thresholds(params: bps_search_params, n_samples: int, n_templates: int) -> np.ndarray:
+    nlev = int(params.nharm_max).bit_length()
+    out = np.zeros(5, np.float64)
+    rc = lib().bps_thresholds(C.byref(params), int(n_samples), int(n_templates), _np_ptr(out))
+    if rc:
+        raise BpsError(rc, "invalid search parameters")
+    return out[:nlev]
+
+
+class Context:
+    """One library context on one CUDA device (wraps bps_create / bps_destroy)."""
+
+    def __init__(self, device: int = 0):
+        h = C.c_void_p()
+        rc = lib().bps_create(C.byref(h), int(device))
+        if rc:
+            raise BpsError(rc, "bps_create(device=%d) failed: no usable CUDA device" % device)
+        self.h = h
+        self.device = device
+
+    def close(self):
+        if getattr(self, "h", None):
+            lib().bps_destroy(self.h)
+            self.h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *a):
+        self.close()
+
+    def _check(self, rc, what):
+        if rc:
+            raise BpsError(rc, "%s: %s" % (what, lib().bps_last_error(self.h).decode()))
+
+    # --- residency ------------------------------------------------------------
+    def load_series(self, x, tsamp: float, dtype: int = BPS_F32) -> int:
+        sid = C.c_int64()
+        on_dev = 0
+        keep = x
+        if hasattr(x, "data_ptr") and hasattr(x, "is_cuda"):
+            if str(x.dtype) != "torch.float32":
+                raise TypeError("series tensor must be float32")
+            x = x.contiguous()
+            keep = x
+            if x.is_cuda:
+                ptr, on_dev = C.c_void_p(x.data_ptr()), 1
+            else:
+                ptr = C.c_void_p(x.data_ptr())
+            n = x.numel()
+        else:
+            keep = np.ascontiguousarray(x, np.float32)
+            ptr, n = _np_ptr(keep), keep.size
+        rc = lib().bps_load_series(self.h, ptr, n, float(tsamp), int(dtype), on_dev, C.byref(sid))
+        self._check(rc, "bps_load_series")
+        if on_dev and dtype == BPS_F32:
+            # borrowed device memory: keep the tensor alive with the id
+            self.__dict__.setdefault("_borrowed", {})[sid.value] = keep
+        return sid.value
+
+    def load_bank(self, bank) -> int:
+        b = np.ascontiguousarray(np.asarray(bank, np.float64).reshape(-1, 5))
+        bid = C.c_int64()
+        rc = lib().bps_load_bank(self.h, _np_ptr(b), b.shape[0], C.byref(bid))
+        self._check(rc, "bps_load_bank")
+        return bid.value
+
+    def unload(self, id_: int):
+        rc = lib().bps_unload(self.h, int(id_))
+        self._check(rc, "bps_unload")
+        self.__dict__.get("_borrowed", {}).pop(int(id_), None)
+
+    # --- search ------------------------------------------------------------------
+    def search(self, series_id: int, bank_id: int, params: bps_search_params | None = None,
+               stream=None) -> int:
+        params = params or default_params()
+        rid = C.c_int64()
+        rc = lib().bps_search(self.h, int(series_id), int(bank_id), C.byref(params),
+                              _stream_ptr(stream), C.byref(rid))
+        self._check(rc, "bps_search")
+        return rid.value
+
+    def query(self, req_id: int) -> bool:
+        d = C.c_int32()
+        self._check(lib().bps_query(self.h, int(req_id), C.byref(d)), "bps_query")
+        return bool(d.value)
+
+    def fetch_candidates(self, req_id: int, cap: int | None = None, allow_overflow=False):
+        """Returns (candidates structured array sorted by template, nharm, bin; n_total)."""
+        nw, nt = C.c_int64(), C.c_int64()
+        rc = lib().bps_fetch_candidates(self.h, int(req_id), None, 0, C.byref(nw), C.byref(nt))
+        if rc and not (rc == BPS_ERR_CAND_OVERFLOW and allow_overflow):
+            self._check(rc, "bps_fetch_candidates")
+        total = nt.value
+        n = total if cap is None else min(cap, total)
+        out = np.zeros(n, CAND_DTYPE)
+        rc = lib().bps_fetch_candidates(self.h, int(req_id), _np_ptr(out) if n else None, n,
+                                        C.byref(nw), C.byref(nt))
+        if rc and not (rc == BPS_ERR_CAND_OVERFLOW and allow_overflow):
+            self._check(rc, "bps_fetch_candidates")
+        return out[:nw.value], nt.value
+
+    def set_profiling(self, on: bool):
+        self._check(lib().bps_set_profiling(self.h, int(bool(on))), "bps_set_profiling")
+
+    def request_stats(self, req_id: int) -> dict:
+        st = bps_stats()
+        self._check(lib().bps_request_stats(self.h, int(req_id), C.byref(st)), "bps_request_stats")
+        return {"templates": st.templates, "batch": st.batch, "anchor_block": st.anchor_block,
+                "launches": st.launches, "profiled": bool(st.profiled),
+                "stage_launches": {STAGES[i]: st.stage_launches[i] for i in range(6)},
+                "stage_ms": {STAGES[i]: float(st.stage_ms[i]) for i in range(6)}}
+
+    # --- stage entry points --------------------------------------------------------
+    def index_map(self, series_id: int, bank_id: int, template_idx: int, n: int):
+        out = np.empty(n, np.int32)
+        npre = C.c_int64()
+        rc = lib().bps_index_map(self.h, int(series_id), int(bank_id), int(template_idx),
+                                 _np_ptr(out), C.byref(npre))
+        self._check(rc, "bps_index_map")
+        return out, npre.value
+
+    def whitened_spectrum(self, series_id: int, bank_id: int, t0: int, count: int, n: int,
+                          params: bps_search_params | None = None):
+        params = params or default_params()
+        out = np.empty((count, n // 2), np.float32)
+        rc = lib().bps_whitened_spectrum(self.h, int(series_id), int(bank_id), int(t0),
+                                         int(count), C.byref(params), _np_ptr(out))
+        self._check(rc, "bps_whitened_spectrum")
+        return out
+
+    def harmonic_sums(self, series_id: int, bank_id: int, template_idx: int, n: int,
+                      params: bps_search_params | None = None):
+        params = params or default_params()
+        nlev = int(params.nharm_max).bit_length()
+        out = np.empty((nlev, n // 2), np.float32)
+        rc = lib().bps_harmonic_sums(self.h, int(series_id), int(bank_id), int(template_idx),
+                                     C.byref(params), _np_ptr(out))
+        self._check(rc, "bps_harmonic_sums")
+        return out
+
+
+def bps_default_params(p):
+    return lib().bps_default_params(p)
+
+
+def bps_create(out, device):
+    return lib().bps_create(out, device)
+
+
+def bps_destroy(ctx):
+    return lib().bps_destroy(ctx)
+
+
+def bps_load_series(ctx, data, n, tsamp, dtype, on_device, sid):
+    return lib().bps_load_series(ctx, data, n, tsamp, dtype, on_device, sid)
+
+
+def bps_load_bank(ctx, t, count, bid):
+    return lib().bps_load_bank(ctx, t, count, bid)
+
+
+def bps_search(ctx, sid, bid, params, stream, rid):
+    return lib().bps_search(ctx, sid, bid, params, stream, rid)
+
+
+def bps_query(ctx, rid, done):
+    return lib().bps_query(ctx, rid, done)
+
+
+def bps_fetch_candidates(ctx, rid, out, cap, nw, nt):
+    return lib().bps_fetch_candidates(ctx, rid, out, cap, nw, nt)
+
+
+def bps_unload(ctx, id_):
+    return lib().bps_unload(ctx, id_)
+
+
+def bps_last_error(ctx):
+    return lib().bps_last_error(ctx)
+
+
+def bps_index_map(ctx, sid, bid, t, out, npre):
+    return lib().bps_index_map(ctx, sid, bid, t, out, npre)
+
+
+def bps_whitened_spectrum(ctx, sid, bid, t0, count, params, out):
+    return lib().bps_whitened_spectrum(ctx, sid, bid, t0, count, params, out)
+
+
+def bps_harmonic_sums(ctx, sid, bid, t, params, out):
+    return lib().bps_harmonic_sums(ctx, sid, bid, t, params, out)
+
+
+def bps_thresholds(params, n, k, out):
+    return lib().bps_thresholds(params, n, k, out)
+
+
+def bps_set_profiling(ctx, on):
+    return lib().bps_set_profiling(ctx, on)
+
+
+def bps_request_stats(ctx, rid, out):
+    return lib().bps_request_stats(ctx, rid, out)
+
+
+__all__ = ["Context", "BpsError", "default_params", "thresholds", "CAND_DTYPE", "EXPORTED",
+           "STAGES", "bps_template", "bps_candidate", "bps_search_params", "bps_stats"] + EXPORTED + [
+    n for n in dir() if n.startswith("BPS_")]

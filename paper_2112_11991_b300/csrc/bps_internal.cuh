@@ -1,0 +1,101 @@
+// bps_internal.cuh -- device data layouts and launcher declarations shared by the
+// CUDA translation units of libbps (never by the FP64 oracle).
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+namespace bps {
+
+// One orbital template, same layout as the public bps_template (App. A, BT model).
+struct DevTemplate {
+    double porb, tau, phi, omega, ecc;
+};
+
+// Per-anchor constants of the index map (Algorithm 1), evaluated in FP64 at the
+// anchor centre c = b*B + B/2 and rounded to FP32.  For d = m - c the offset is
+//   off(m) = I + f - inc(d),  inc(d) = (Delta_R(t_c + d t_s) - Delta_R(t_c)) / t_s
+// with inc(d) = L d + R(d) and, for the fast path, R(d) ~ q2 d^2 + q3 d^3.
+// Field order: the fast path reads only the first 16 + 4 bytes.
+struct __align__(16) Anchor {
+    int   I;     // floor(O_c), O_c = (Delta_R(0) - Delta_R(t_c)) / t_s
+    float fhi;   // O_c - I, high part
+    float Lhi;   // d inc / d d at d = 0, high part  [samples / sample]
+    float q2;    // (1/2) d^2 inc / dd^2
+    float q3;    // (1/6) d^3 inc / dd^3
+    float flo;   // low part of O_c - I
+    float Llo;   // low part of L
+    float g;     // dE/dd = Omega t_s / (1 - e cos E_c)
+    float esE;   // e sin E_c
+    float ecE;   // e cos E_c
+    float invD;  // 1 / (1 - e cos E_c)
+    float KBc;   // (tau/t_s) * dBT/dE at E_c
+    float KAc;   // (tau/t_s) * (cos E_c sin w + sqrt(1-e^2) sin E_c cos w)
+    float pad0, pad1, pad2;
+};
+static_assert(sizeof(Anchor) == 64, "Anchor must be 64 bytes");
+
+// Problem geometry of one search (host-built, passed by value to kernels).
+struct Plan {
+    int64_t n;      // real samples N (power of two)
+    int64_t M;      // N/2 complex points of the packed FFT
+    int logn, logM;
+    int logR, logC; // M = R * C (four-step: R-point column FFTs, C-point row FFTs)
+    int logG;       // columns per CTA in pass 1
+    int logB;       // anchor block length B (samples)
+    int64_t nanchor;// N / B
+    int logW;       // whitening block W (bins)
+    int nharm;      // nharm_max (power of two <= 16)
+    int lognh;
+    int nlev;       // log2(nharm) + 1
+    double tsamp;
+};
+
+// Thresholds of the harmonic levels, by value.
+struct Thr {
+    float v[5];
+};
+
+// Candidate record: same layout as the public bps_candidate.
+struct Cand {
+    uint32_t tidx;
+    uint16_t nharm;
+    uint16_t flags;
+    uint32_t bin;
+    float power;
+};
+
+// Series storage descriptor.
+struct SeriesView {
+    const float* f32;          // FP32 samples (or nullptr)
+    const uint16_t* f16;       // FP16 samples (or nullptr)
+    const float* scale;        // per-4096-sample scale for FP16
+    float fill;                // mean of the series (value for out-of-range samples)
+};
+
+// Launchers (stream-ordered, return cudaGetLastError()).
+cudaError_t launch_twiddle_init(float2* tw4096, cudaStream_t s);
+cudaError_t launch_anchors(const DevTemplate* bank, int64_t t0, int nt, const Plan& p,
+                           Anchor* out, cudaStream_t s);
+cudaError_t launch_index_map(const Anchor* anc, const Plan& p, int32_t* idx,
+                             unsigned long long* n_precise, cudaStream_t s);
+cudaError_t launch_resample(const SeriesView& x, const Anchor* anc, int nt, const Plan& p,
+                            float* out, cudaStream_t s);
+cudaError_t launch_pass1(const SeriesView& x, const Anchor* anc, int nt, const Plan& p,
+                         const float2* tw, float2* Y, cudaStream_t s);
+cudaError_t launch_pass2(const float2* Y, int nt, const Plan& p, const float2* tw,
+                         float* P, cudaStream_t s);
+cudaError_t launch_power_from_r2c(const float2* X, int nt, const Plan& p, float* P,
+                                  cudaStream_t s);
+cudaError_t launch_block_median(const float* P, int nt, const Plan& p, float* scale,
+                                cudaStream_t s);
+cudaError_t launch_whitened(const float* P, const float* scale, int nt, const Plan& p,
+                            float* out, cudaStream_t s);
+cudaError_t launch_harmsum(const float* P, const float* scale, int nt, int64_t tidx0,
+                           const Plan& p, const Thr& thr, Cand* cands, int64_t cap,
+                           unsigned long long* count, float* s_out, cudaStream_t s);
+cudaError_t launch_series_stats(const float* x, int64_t n, double* sum, cudaStream_t s);
+cudaError_t launch_f16_pack(const float* x, int64_t n, uint16_t* h, float* scale,
+                            cudaStream_t s);
+
+}  // namespace bps

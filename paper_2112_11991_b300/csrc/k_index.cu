@@ -1,0 +1,222 @@
+// k_index.cu -- FP64 anchor kernel, standalone index map, plain resampling
+// gather, series statistics and FP16 packing.
+//
+// Anchor kernel (App. A.1, Algorithm 1; Kepler's equation, Sec. 2.1; BT Roemer
+// delay, App. A): for every template and every anchor block of B samples it
+// reduces the mean anomaly M = Omega t_c + alpha in FP64, solves Kepler's
+// equation by FP64 Newton iteration, evaluates the BT delay and the zero offset
+// t_0 = Delta_R(0)/t_s, and stores the FP32 constants the per-sample
+// evaluation (index_map.cuh) needs.  FP64 work is N/B Kepler solves per
+// template (B is chosen by the planner, typically 4096 samples).
+#include <cmath>
+
+#include "bps_internal.cuh"
+#include "index_map.cuh"
+
+namespace bps {
+
+namespace {
+
+constexpr double kTwoPi = 6.283185307179586476925286766559;
+
+__device__ double reduce_2pi(double x)
+{
+    double r = x - kTwoPi * floor(x / kTwoPi);
+    if (r < 0.0) r += kTwoPi;
+    if (r >= kTwoPi) r -= kTwoPi;
+    return r;
+}
+
+// Kepler's equation E - e sin E = M by Newton iteration from E0 = M + e sin M.
+__device__ double kepler64(double M, double e)
+{
+    double E = M + e * sin(M);
+    for (int it = 0; it < 40; ++it) {
+        double s, c;
+        sincos(E, &s, &c);
+        const double dE = (E - e * s - M) / (1.0 - e * c);
+        E -= dE;
+        if (fabs(dE) < 1e-15) break;
+    }
+    return E;
+}
+
+__global__ void k_anchors(const DevTemplate* __restrict__ bank, int64_t t0, Plan p,
+                          Anchor* __restrict__ out)
+{
+    __shared__ double s_delta0;
+    const int tl = blockIdx.y;
+    const DevTemplate T = bank[t0 + tl];
+    const double e = T.ecc;
+    double sw, cw;
+    sincos(T.omega, &sw, &cw);
+    const double rt = sqrt(1.0 - e * e);
+    if (threadIdx.x == 0) {
+        // zero offset of Algorithm 1: M = alpha at t = 0
+        const double E0 = kepler64(reduce_2pi(T.phi), e);
+        double s0, c0;
+        sincos(E0, &s0, &c0);
+        s_delta0 = T.tau * ((c0 - e) * sw + rt * s0 * cw);
+    }
+    __syncthreads();
+    const int64_t b = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (b >= p.nanchor) return;
+    const double Om = kTwoPi / T.porb;
+    const int64_t mc = (b << p.logB) + (1ll << (p.logB - 1));
+    const double tc = (double)mc * p.tsamp;
+    const double M = reduce_2pi(Om * tc + T.phi);
+    const double E = kepler64(M, e);
+    double sE, cE;
+    sincos(E, &sE, &cE);
+    const double Dc = T.tau * ((cE - e) * sw + rt * sE * cw);
+    const double O = (s_delta0 - Dc) / p.tsamp;
+    const double If = floor(O);
+    const double f = O - If;
+    const double K = T.tau / p.tsamp;
+    const double ws = Om * p.tsamp;
+    const double D = 1.0 - e * cE;
+    const double g = ws / D;
+    const double Ac = cE * sw + rt * sE * cw;   // -(d^2 BT / dE^2) - e sin w
+    const double Bc = -sE * sw + rt * cE * cw;  // d BT / dE
+    const double L = K * Bc * g;
+    const double u2 = -e * sE * g * g / (2.0 * D);
+    const double u3 = -(e * sE * g * u2 + e * cE * g * g * g / 6.0) / D;
+    const double q2 = K * (Bc * u2 - Ac * g * g / 2.0);
+    const double q3 = K * (Bc * u3 - Ac * g * u2 - Bc * g * g * g / 6.0);
+    Anchor a;
+    a.I = (int)If;
+    a.fhi = (float)f;
+    a.flo = (float)(f - (double)a.fhi);
+    a.Lhi = (float)L;
+    a.Llo = (float)(L - (double)a.Lhi);
+    a.q2 = (float)q2;
+    a.q3 = (float)q3;
+    a.g = (float)g;
+    a.esE = (float)(e * sE);
+    a.ecE = (float)(e * cE);
+    a.invD = (float)(1.0 / D);
+    a.KBc = (float)(K * Bc);
+    a.KAc = (float)(K * Ac);
+    a.pad0 = a.pad1 = a.pad2 = 0.f;
+    out[(int64_t)tl * p.nanchor + b] = a;
+}
+
+__global__ void k_index_map(const Anchor* __restrict__ anc, Plan p, int32_t* __restrict__ idx,
+                            unsigned long long* __restrict__ n_precise)
+{
+    const int64_t m = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    bool precise = false;
+    if (m < p.n) {
+        const int64_t b = anchor_of(m, p.logB);
+        const Anchor a = anc[b];
+        const int d = (int)(m - anchor_centre(b, p.logB));
+        const int k = off_round(a, d, precise);
+        idx[m] = (int32_t)(m + a.I + k);
+    }
+    const unsigned mask = __ballot_sync(0xffffffffu, precise);
+    if ((threadIdx.x & 31) == 0 && mask) atomicAdd(n_precise, (unsigned long long)__popc(mask));
+}
+
+__global__ void k_resample(SeriesView x, const Anchor* __restrict__ anc, Plan p,
+                           float* __restrict__ out)
+{
+    const int tl = blockIdx.y;
+    const int64_t m = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (m >= p.n) return;
+    const Anchor* at = anc + (int64_t)tl * p.nanchor;
+    const int64_t b = anchor_of(m, p.logB);
+    const Anchor a = at[b];
+    bool precise;
+    const int k = off_round(a, (int)(m - anchor_centre(b, p.logB)), precise);
+    out[(int64_t)tl * p.n + m] = gather_sample(x, p.n, m + a.I + k);
+}
+
+__global__ void k_series_sum(const float* __restrict__ x, int64_t n, double* __restrict__ sum)
+{
+    __shared__ double part[32];
+    double s = 0.0;
+    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n;
+         i += (int64_t)gridDim.x * blockDim.x)
+        s += (double)x[i];
+    for (int o = 16; o > 0; o >>= 1) s += __shfl_down_sync(0xffffffffu, s, o);
+    if ((threadIdx.x & 31) == 0) part[threadIdx.x >> 5] = s;
+    __syncthreads();
+    if (threadIdx.x < 32) {
+        s = (threadIdx.x < (blockDim.x >> 5)) ? part[threadIdx.x] : 0.0;
+        for (int o = 16; o > 0; o >>= 1) s += __shfl_down_sync(0xffffffffu, s, o);
+        if (threadIdx.x == 0) atomicAdd(sum, s);
+    }
+}
+
+// FP16 storage with one power-of-two scale per 4096 samples: s = 2^ceil(log2 max|x|),
+// h = half(x / s) (division by s is exact, only the FP16 rounding loses bits).
+__global__ void k_f16_pack(const float* __restrict__ x, int64_t n, uint16_t* __restrict__ h,
+                           float* __restrict__ scale)
+{
+    __shared__ float wmax[32];
+    __shared__ float s_scale;
+    const int64_t base = (int64_t)blockIdx.x << 12;
+    float mx = 0.f;
+    for (int i = threadIdx.x; i < 4096; i += blockDim.x)
+        if (base + i < n) mx = fmaxf(mx, fabsf(x[base + i]));
+    for (int o = 16; o > 0; o >>= 1) mx = fmaxf(mx, __shfl_down_sync(0xffffffffu, mx, o));
+    if ((threadIdx.x & 31) == 0) wmax[threadIdx.x >> 5] = mx;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        float m = 0.f;
+        for (int w = 0; w < (int)(blockDim.x >> 5); ++w) m = fmaxf(m, wmax[w]);
+        int ex = 0;
+        if (m > 0.f) {
+            const float fr = frexpf(m, &ex);  // m = fr * 2^ex, fr in [0.5, 1)
+            if (fr == 0.5f) ex -= 1;           // exact power of two: 2^(ex-1) = m
+        }
+        s_scale = ldexpf(1.f, ex);
+        scale[blockIdx.x] = s_scale;
+    }
+    __syncthreads();
+    const float inv = 1.f / s_scale;  // exact: power of two
+    for (int i = threadIdx.x; i < 4096; i += blockDim.x)
+        if (base + i < n) h[base + i] = __half_as_ushort(__float2half_rn(x[base + i] * inv));
+}
+
+}  // namespace
+
+cudaError_t launch_anchors(const DevTemplate* bank, int64_t t0, int nt, const Plan& p,
+                           Anchor* out, cudaStream_t s)
+{
+    dim3 grid((unsigned)((p.nanchor + 127) / 128), (unsigned)nt);
+    k_anchors<<<grid, 128, 0, s>>>(bank, t0, p, out);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_index_map(const Anchor* anc, const Plan& p, int32_t* idx,
+                             unsigned long long* n_precise, cudaStream_t s)
+{
+    k_index_map<<<(unsigned)((p.n + 255) / 256), 256, 0, s>>>(anc, p, idx, n_precise);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_resample(const SeriesView& x, const Anchor* anc, int nt, const Plan& p,
+                            float* out, cudaStream_t s)
+{
+    dim3 grid((unsigned)((p.n + 255) / 256), (unsigned)nt);
+    k_resample<<<grid, 256, 0, s>>>(x, anc, p, out);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_series_stats(const float* x, int64_t n, double* sum, cudaStream_t s)
+{
+    int blocks = (int)((n + 1023) / 1024);
+    if (blocks > 148 * 8) blocks = 148 * 8;
+    k_series_sum<<<blocks, 1024, 0, s>>>(x, n, sum);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_f16_pack(const float* x, int64_t n, uint16_t* h, float* scale,
+                            cudaStream_t s)
+{
+    k_f16_pack<<<(unsigned)((n + 4095) >> 12), 256, 0, s>>>(x, n, h, scale);
+    return cudaGetLastError();
+}
+
+}  // namespace bps

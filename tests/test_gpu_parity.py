@@ -1,0 +1,278 @@
+"""GPU parity: the CUDA path (through the C ABI) against the FP64 oracle, element
+by element, on seeded inputs at sizes the oracle finishes in seconds (several
+FFT tiles and anchor blocks, ragged orbits), plus edge cases.  Tolerances are
+in tests/gpu_common.py."""
+import math
+
+import numpy as np
+import pytest
+
+import synth
+from gpu_common import PW_TOL, compare_candidates, pw_close, s_close
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def bps():
+    import torch
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    from paper_2112_11991_b300 import build
+    build.build()
+    import paper_2112_11991_b300 as m
+    return m
+
+
+@pytest.fixture(scope="module")
+def ctx(bps):
+    c = bps.Context(0)
+    yield c
+    c.close()
+
+
+@pytest.fixture(scope="module")
+def w1():
+    return synth.plain_circular()
+
+
+ORBITS = [
+    (400.0, 0.2, 1.0, 0.0, 0.0),       # the injected orbit of the 2^20 workload
+    (200.0, 0.4, 5.9, 0.0, 0.0),       # fastest / widest circular corner
+    (670.0, 0.05, 3.3, 0.0, 0.0),
+    (25.0, 0.3, 2.0, 1.1, 0.3),        # fast eccentric orbit
+    (300.0, 0.5, 2.0, 1.1, 0.3),
+    (5000.0, 20.0, 0.4, 4.0, 0.09),    # wide elliptical, large tau
+    (400.0, 0.0, 1.0, 0.0, 0.0),       # tau = 0: identity
+]
+
+
+@pytest.mark.parametrize("logn,ts", [(11, 64e-6), (16, 64e-6), (20, 64e-6), (20, 128e-6)])
+def test_index_map_bitexact(bps, ctx, orc, logn, ts):
+    n = 1 << logn
+    x = synth.noise(n, 3)
+    sid = ctx.load_series(x, ts)
+    bid = ctx.load_bank(np.array(ORBITS))
+    total_near = 0
+    for t, tm in enumerate(ORBITS):
+        gi, npre = ctx.index_map(sid, bid, t, n)
+        oi, off, near = orc.index_map(tm, n, ts)
+        bad = gi.astype(np.int64) != oi
+        assert not np.any(bad & ~near), (t, np.flatnonzero(bad & ~near)[:10])
+        total_near += int(near.sum())
+        if tm[1] == 0.0:
+            assert np.array_equal(gi, np.arange(n)) and npre == 0
+    ctx.unload(sid)
+    ctx.unload(bid)
+
+
+@pytest.mark.parametrize("mode", [0, 1])
+@pytest.mark.parametrize("logn", [11, 14, 17, 20])
+def test_whitened_spectrum_parity(bps, ctx, orc, logn, mode):
+    n = 1 << logn
+    ts = 64e-6
+    p = synth.Pulsar(period_s=0.02, porb_s=90.0, tau_lts=0.1, phi_rad=0.3, amp=0.5)
+    x = synth.inject(synth.noise(n, 40 + logn), ts, p)
+    tms = [p.orbit(), (60.0, 0.3, 4.0, 2.0, 0.2), (1e4, 0.0, 0.0, 0.0, 0.0)]
+    sid = ctx.load_series(x, ts)
+    bid = ctx.load_bank(np.array(tms))
+    W = min(1024, n // 2)
+    prm = bps.default_params(whiten_block=W, mode=mode)
+    pw = ctx.whitened_spectrum(sid, bid, 0, len(tms), n, prm)
+    for t, tm in enumerate(tms):
+        r = orc.search_template(x, ts, tm, whiten_block=W, want_arrays=True)
+        assert pw_close(pw[t], r["Pw"]) <= PW_TOL, (t, pw_close(pw[t], r["Pw"]))
+    ctx.unload(sid)
+    ctx.unload(bid)
+
+
+@pytest.mark.parametrize("nharm", [1, 2, 4, 8, 16])
+def test_harmonic_sums_parity(bps, ctx, orc, w1, nharm):
+    n = 1 << 18
+    x = w1.series[:n].copy()
+    sid = ctx.load_series(x, w1.tsamp)
+    tm = w1.pulsars[0].orbit()
+    bid = ctx.load_bank(np.array([tm]))
+    prm = bps.default_params(nharm_max=nharm)
+    S = ctx.harmonic_sums(sid, bid, 0, n, prm)
+    r = orc.search_template(x, w1.tsamp, tm, nharm_max=nharm, want_arrays=True)
+    for L in range(S.shape[0]):
+        assert s_close(S[L], r["S"][L], 1 << L) <= PW_TOL, (L, s_close(S[L], r["S"][L], 1 << L))
+    ctx.unload(sid)
+    ctx.unload(bid)
+
+
+@pytest.mark.parametrize("mode", [0, 1])
+def test_search_candidates_workload_2p20(bps, ctx, orc, w1, mode):
+    """The whole 2^20-sample, 32-template circular workload: GPU candidates equal
+    the oracle's, and the injected pulsar is found under its true orbit."""
+    sid = ctx.load_series(w1.series, w1.tsamp)
+    bid = ctx.load_bank(w1.bank)
+    prm = bps.default_params(mode=mode)
+    rid = ctx.search(sid, bid, prm)
+    gc, total = ctx.fetch_candidates(rid)
+    assert total == gc.size
+    oc, counts, _ = orc.search(w1.series, w1.tsamp, w1.bank, cap_per=1 << 14)
+    thr = bps.thresholds(prm, w1.n, w1.bank.shape[0])
+    matched, excused = compare_candidates(gc, oc, thr)
+    assert matched > 1000
+    p = w1.pulsars[0]
+    ti = w1.true_idx[0]
+    top = gc[(gc["template_idx"] == ti) & (gc["nharm"] == 16)]
+    kbest = int(top["bin"][np.argmax(top["power"])])
+    assert abs(kbest - round(16 * w1.n * w1.tsamp / p.period_s)) <= 1
+    best_t = {}
+    for c in gc[gc["nharm"] == 16]:
+        best_t[int(c["template_idx"])] = max(best_t.get(int(c["template_idx"]), 0), float(c["power"]))
+    assert max(best_t, key=best_t.get) == ti
+    ctx.unload(rid)
+    ctx.unload(sid)
+    ctx.unload(bid)
+
+
+def test_batch_invariance(bps, ctx, w1):
+    n = 1 << 18
+    x = w1.series[:n].copy()
+    sid = ctx.load_series(x, w1.tsamp)
+    bid = ctx.load_bank(w1.bank[:7])
+    res = []
+    for b in [1, 3, 0]:
+        rid = ctx.search(sid, bid, bps.default_params(batch=b))
+        c, _ = ctx.fetch_candidates(rid)
+        res.append(c)
+        ctx.unload(rid)
+    for c in res[1:]:
+        assert np.array_equal(c, res[0])
+    ctx.unload(sid)
+    ctx.unload(bid)
+
+
+@pytest.mark.parametrize("W,nharm,sigma", [(32, 4, 5.0), (8192, 16, 6.0), (256, 1, 4.5)])
+def test_variants_parity(bps, ctx, orc, W, nharm, sigma):
+    n = 1 << 17
+    ts = 64e-6
+    p = synth.Pulsar(period_s=0.03, porb_s=50.0, tau_lts=0.05, phi_rad=2.5, amp=0.5)
+    x = synth.inject(synth.noise(n, 77), ts, p)
+    bank = np.array([p.orbit(), (80.0, 0.1, 1.0, 0.0, 0.0), (40.0, 0.06, 2.0, 0.5, 0.05)])
+    sid = ctx.load_series(x, ts)
+    bid = ctx.load_bank(bank)
+    prm = bps.default_params(whiten_block=W, nharm_max=nharm, sigma_thr=sigma)
+    gc, _ = ctx.fetch_candidates(ctx.search(sid, bid, prm))
+    oc, _, _ = orc.search(x, ts, bank, nharm_max=nharm, whiten_block=W, sigma=sigma, cap_per=1 << 15)
+    compare_candidates(gc, oc, bps.thresholds(prm, n, 3))
+    ctx.unload(sid)
+    ctx.unload(bid)
+
+
+def test_minimum_size(bps, ctx, orc):
+    n, ts = 1 << 11, 64e-6
+    x = synth.noise(n, 5)
+    x[::50] += 3.0
+    bank = np.array([(30.0, 0.001, 1.0, 0.0, 0.0), (30.0, 0.0, 0.0, 0.0, 0.0)])
+    sid = ctx.load_series(x, ts)
+    bid = ctx.load_bank(bank)
+    prm = bps.default_params(whiten_block=32, sigma_thr=4.0)
+    gc, _ = ctx.fetch_candidates(ctx.search(sid, bid, prm))
+    oc, _, _ = orc.search(x, ts, bank, whiten_block=32, sigma=4.0)
+    m, _ = compare_candidates(gc, oc, bps.thresholds(prm, n, 2))
+    assert m > 0
+    pw = ctx.whitened_spectrum(sid, bid, 0, 2, n, prm)
+    r = orc.search_template(x, ts, bank[0], whiten_block=32, want_arrays=True)
+    assert pw_close(pw[0], r["Pw"]) <= PW_TOL
+
+
+def test_zero_series_has_no_candidates(bps, ctx):
+    n = 1 << 14
+    sid = ctx.load_series(np.zeros(n, np.float32), 64e-6)
+    bid = ctx.load_bank(np.array([(100.0, 0.1, 0.0, 0.0, 0.0)]))
+    gc, total = ctx.fetch_candidates(ctx.search(sid, bid))
+    assert total == 0
+    pw = ctx.whitened_spectrum(sid, bid, 0, 1, n)
+    assert np.all(pw == 0)
+
+
+def test_invalid_arguments(bps, ctx):
+    with pytest.raises(bps.BpsError) as e:
+        ctx.load_series(np.zeros(3000, np.float32), 64e-6)
+    assert e.value.code == bps.BPS_ERR_INVALID_ARG
+    with pytest.raises(bps.BpsError):
+        ctx.load_series(np.zeros(1 << 10, np.float32), 64e-6)
+    with pytest.raises(bps.BpsError):
+        ctx.load_series(np.zeros(1 << 12, np.float32), 0.0)
+    for bad in [(0.0, 0.1, 0, 0, 0), (100.0, -1.0, 0, 0, 0), (100.0, 0.1, 0, 0, 1.0),
+                (100.0, 0.1, float("nan"), 0, 0)]:
+        with pytest.raises(bps.BpsError):
+            ctx.load_bank(np.array([bad]))
+    sid = ctx.load_series(np.zeros(1 << 12, np.float32), 64e-6)
+    bid = ctx.load_bank(np.array([(100.0, 0.1, 0, 0, 0)]))
+    with pytest.raises(bps.BpsError):
+        ctx.search(sid, 999999)
+    with pytest.raises(bps.BpsError):
+        ctx.search(sid, bid, bps.default_params(whiten_block=4096))  # > n/2
+    fast = ctx.load_bank(np.array([(1.0, 50.0, 0, 0, 0)]))  # beyond the FP32 index-map envelope
+    with pytest.raises(bps.BpsError) as e:
+        ctx.search(sid, fast)
+    assert e.value.code == bps.BPS_ERR_UNSUPPORTED
+    with pytest.raises(bps.BpsError):
+        ctx.unload(123456789)
+
+
+def test_candidate_overflow(bps, ctx, w1):
+    n = 1 << 18
+    sid = ctx.load_series(w1.series[:n].copy(), w1.tsamp)
+    bid = ctx.load_bank(w1.bank[:4])
+    rid = ctx.search(sid, bid, bps.default_params(sigma_thr=3.0))
+    full, total = ctx.fetch_candidates(rid)
+    rid2 = ctx.search(sid, bid, bps.default_params(sigma_thr=3.0, cand_cap=10))
+    with pytest.raises(bps.BpsError) as e:
+        ctx.fetch_candidates(rid2)
+    assert e.value.code == bps.BPS_ERR_CAND_OVERFLOW
+    part, total2 = ctx.fetch_candidates(rid2, allow_overflow=True)
+    assert total2 == total and part.size == 10
+    assert set(map(tuple, part[["template_idx", "nharm", "bin"]].tolist())) <= \
+        set(map(tuple, full[["template_idx", "nharm", "bin"]].tolist()))
+
+
+def test_device_pointer_series_and_stream(bps, ctx, w1):
+    import torch
+    n = 1 << 18
+    x = w1.series[:n].copy()
+    bid = ctx.load_bank(w1.bank[:5])
+    s_host = ctx.load_series(x, w1.tsamp)
+    xt = torch.from_numpy(x).cuda()
+    s_dev = ctx.load_series(xt, w1.tsamp)
+    st = torch.cuda.Stream()
+    a, _ = ctx.fetch_candidates(ctx.search(s_host, bid))
+    rid = ctx.search(s_dev, bid, stream=st)
+    b, _ = ctx.fetch_candidates(rid)
+    assert np.array_equal(a, b)
+
+
+def test_query_is_nonblocking_and_completes(bps, ctx, w1):
+    import time
+    sid = ctx.load_series(w1.series, w1.tsamp)
+    bid = ctx.load_bank(w1.bank)
+    rid = ctx.search(sid, bid)
+    t0 = time.time()
+    while not ctx.query(rid):
+        assert time.time() - t0 < 60
+        time.sleep(0.001)
+    c, total = ctx.fetch_candidates(rid)
+    assert total > 0
+
+
+def test_fp16_storage_error_bounded(bps, ctx, orc, w1):
+    """FP16 series with a power-of-two scale per 4096 samples, FP32 FFT: the
+    whitened power differs from the FP64 oracle (fed the original FP32 series)
+    by the FP16 rounding of the samples only; the pulsar's top candidates agree."""
+    n = 1 << 20
+    sid = ctx.load_series(w1.series, w1.tsamp, dtype=bps.BPS_F16_SCALED)
+    ti = w1.true_idx[0]
+    bid = ctx.load_bank(w1.bank[ti:ti + 1])
+    pw = ctx.whitened_spectrum(sid, bid, 0, 1, n)[0]
+    r = orc.search_template(w1.series, w1.tsamp, w1.bank[ti], want_arrays=True)
+    err = np.abs(pw - r["Pw"]) / np.maximum(1.0, r["Pw"])
+    assert err.max() < 5e-3, err.max()
+    S = ctx.harmonic_sums(sid, bid, 0, n)
+    for L in range(5):
+        assert int(np.argmax(S[L])) == int(np.argmax(r["S"][L]))
