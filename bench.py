@@ -40,6 +40,7 @@ UNIT = "templates/s"
 STAGE_BYTES_PER_N = {"pass1": 8.0, "pass2": 6.0, "median": 2.0, "harmsum": 2.0,
                      "power": 4.0 + 2.0, "anchors": 0.0}
 PATH_BYTES_PER_N = 8.0
+CAND_CAP = 1 << 22
 
 
 def parse():
@@ -256,11 +257,12 @@ def main():
     flush = torch.empty(256 << 20, dtype=torch.uint8, device=dev)
 
     def timed_steps(mode, steps, warmup, profile):
-        prm = bps.default_params(mode=mode, batch=args.batch if mode == 0 else 0)
+        prm = bps.default_params(mode=mode, batch=args.batch if mode == 0 else 0,
+                                 cand_cap=CAND_CAP)
         ctx.set_profiling(False)
         for _ in range(warmup):
             rid = ctx.search(sid, bid, prm, stream=stream)
-            ctx.fetch_candidates(rid, cap=0)
+            ctx.fetch_candidates(rid, cap=0, allow_overflow=True)
             ctx.unload(rid)
         ctx.set_profiling(profile)
         ms, stats, ncand = [], [], 0
@@ -276,7 +278,7 @@ def main():
             b.synchronize()
             ms.append(a.elapsed_time(b))
             stats.append(ctx.request_stats(rid))
-            _, tot = ctx.fetch_candidates(rid, cap=0)
+            _, tot = ctx.fetch_candidates(rid, cap=0, allow_overflow=True)
             ncand = tot
             ctx.unload(rid)
         torch.cuda.synchronize(dev)
@@ -304,14 +306,14 @@ def main():
     pinned = torch.from_numpy(w.series).pin_memory()
     e2e_ms = []
     d2h = 0
-    prm = bps.default_params(batch=args.batch)
+    prm = bps.default_params(batch=args.batch, cand_cap=CAND_CAP)
     for i in range(args.warmup + args.steps):
         torch.cuda.synchronize(dev)
         t0 = time.perf_counter()
         s2 = ctx.load_series(pinned, w.tsamp)
         b2 = ctx.load_bank(bank)
         rid = ctx.search(s2, b2, prm, stream=stream)
-        c, tot = ctx.fetch_candidates(rid)
+        c, tot = ctx.fetch_candidates(rid, allow_overflow=True)
         ctx.unload(rid)
         ctx.unload(s2)
         ctx.unload(b2)

@@ -88,7 +88,7 @@ def lib():
         L.orc_snmin.argtypes = [d]
         L.orc_search_template.restype = i64
         L.orc_search_template.argtypes = [vp, i64, d, d, C.POINTER(Template), i64,
-                                          i32, i64, vp, vp, i64, vp, vp, vp, vp]
+                                          i32, i64, vp, vp, i64, vp, vp, vp, vp, vp]
         L.orc_search.restype = i32
         L.orc_search.argtypes = [vp, i64, d, d, vp, vp, i64, i32, i64, vp,
                                  vp, i64, vp, vp, i32]
@@ -216,10 +216,11 @@ def nlevels_for(nharm_max: int) -> int:
 
 def search_template(x, tsamp, tmpl, *, nharm_max=16, whiten_block=1024,
                     sigma=6.0, thr=None, fill=None, template_idx=0,
-                    cap=1 << 20, want_arrays=False):
+                    cap=1 << 20, want_arrays=False, idx_in=None):
     """One template through the whole path.  Returns a dict with 'cands'
     (structured numpy array: template_idx, nharm, near_thr, bin, power),
-    'n_found', 'n_near' and, if want_arrays, 'idx', 'Pw', 'S'."""
+    'n_found', 'n_near' and, if want_arrays, 'idx', 'Pw', 'S'.  idx_in replaces
+    the index map (a map validated against index_map(), see bps_oracle.c)."""
     x = np.ascontiguousarray(x, np.float32)
     n = x.size
     nl = nlevels_for(nharm_max)
@@ -234,7 +235,8 @@ def search_template(x, tsamp, tmpl, *, nharm_max=16, whiten_block=1024,
         _ptr(x), n, float(tsamp), fill, C.byref(as_template(tmpl)), int(template_idx),
         nl, int(whiten_block), _ptr(thr), C.cast(out, C.c_void_p), cap,
         _ptr(idx) if want_arrays else None, _ptr(Pw) if want_arrays else None,
-        _ptr(S) if want_arrays else None, C.byref(n_near))
+        _ptr(S) if want_arrays else None, C.byref(n_near),
+        _ptr(np.ascontiguousarray(idx_in, np.int64)) if idx_in is not None else None)
     cands = _cands_to_numpy(out, min(found, cap))
     res = {"cands": cands, "n_found": int(found), "n_near": int(n_near.value), "thr": thr}
     if want_arrays:

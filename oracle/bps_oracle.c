@@ -300,7 +300,10 @@ double orc_snmin(double ntrials)
 /* ------------------------------------------------------------------------- */
 /* One template, the whole path (App. A): index map -> gather -> FFT ->        */
 /* power -> de-redden -> harmonic sum -> threshold.  Optional outputs (may be  */
-/* NULL): idx[n], Pw[n/2], S[nlevels * n/2].                                   */
+/* NULL): idx[n], Pw[n/2], S[nlevels * n/2].  idx_in (may be NULL) replaces    */
+/* the index map: offsets within 1e-6 of a half-integer have two admissible   */
+/* roundings, and parity tests supply a map they have validated against       */
+/* orc_index_map sample by sample.                                            */
 /* Returns the number of candidates found (writes at most cap).               */
 /* ------------------------------------------------------------------------- */
 int64_t orc_search_template(const float *x, int64_t n, double tsamp, double fill,
@@ -308,7 +311,7 @@ int64_t orc_search_template(const float *x, int64_t n, double tsamp, double fill
                             int nlevels, int64_t W, const double *thr,
                             orc_candidate *out, int64_t cap,
                             int64_t *idx_out, double *Pw_out, double *S_out,
-                            int64_t *n_near)
+                            int64_t *n_near, const int64_t *idx_in)
 {
     int64_t nb = n / 2;
     int64_t *idx = idx_out ? idx_out : (int64_t *)malloc(sizeof(int64_t) * (size_t)n);
@@ -319,6 +322,7 @@ int64_t orc_search_template(const float *x, int64_t n, double tsamp, double fill
     double *S = S_out ? S_out : (double *)malloc(sizeof(double) * (size_t)nb * (size_t)nlevels);
 
     orc_index_map(tp, n, tsamp, idx, NULL, near);
+    if (idx_in) memcpy(idx, idx_in, sizeof(int64_t) * (size_t)n);
     if (n_near) {
         int64_t c = 0;
         for (int64_t j = 0; j < n; ++j) c += near[j];
@@ -379,7 +383,7 @@ static void *orc_worker(void *arg)
         p->counts[t] = orc_search_template(
             p->x, p->n, p->tsamp, p->fill, &p->bank[t], p->tidx ? p->tidx[t] : t,
             p->nlevels, p->W, p->thr, p->out ? p->out + t * p->cap_per : NULL,
-            p->cap_per, NULL, NULL, NULL, &nn);
+            p->cap_per, NULL, NULL, NULL, &nn, NULL);
         if (p->n_near) p->n_near[t] = nn;
     }
     return NULL;

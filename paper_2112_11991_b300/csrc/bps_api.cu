@@ -172,8 +172,9 @@ void thresholds(const bps_search_params* pr, int64_t n, int64_t K, double* out)
 }
 
 // Geometry + anchor block length.  The anchor block B is the largest power of two
-// (<= 8192) for which the FP32 fast path stays well inside its 1e-4 guard:
-// |inc| <= 32 samples, quadratic term <= 0.25 sample, quartic remainder <= 1e-5.
+// (<= 8192) for which, for every template, the FP32 fast path stays well inside its
+// 1e-4 guard: |inc| <= 32 samples, quadratic term <= 0.25 sample, quartic
+// remainder <= 1e-5 sample (h = B/2 the largest distance to the anchor centre).
 int make_plan(bps_ctx* ctx, const Series& s, const Bank& b, const bps_search_params& pr,
               Plan& p)
 {
@@ -189,18 +190,21 @@ int make_plan(bps_ctx* ctx, const Series& s, const Bank& b, const bps_search_par
     p.lognh = ilog2(pr.nharm_max);
     p.nlev = p.lognh + 1;
     p.tsamp = s.tsamp;
-    double Kmax = 0.0, gmax = 0.0;
+    // per template: K = tau/t_s, g = Omega t_s / (1 - e) (bound on dE/dsample)
+    double kg1 = 0.0, kg2 = 0.0, kg4 = 0.0, Kmax = 0.0, gmax = 0.0;
     for (const auto& t : b.h) {
         const double K = t.tau_lts / s.tsamp;
         const double g = (2.0 * M_PI / t.porb_s) * s.tsamp / (1.0 - t.ecc);
+        kg1 = std::max(kg1, K * g);
+        kg2 = std::max(kg2, K * g * g);
+        kg4 = std::max(kg4, K * g * g * g * g);
         Kmax = std::max(Kmax, K);
         gmax = std::max(gmax, K > 0 ? g : 0.0);
     }
     int logB = std::min(13, p.logn);
     for (; logB >= 6; --logB) {
         const double h = (double)(1 << (logB - 1));
-        const double gh = gmax * h;
-        if (Kmax * gh <= 32.0 && Kmax * gh * gh <= 0.25 && Kmax * gh * gh * gh * gh <= 1e-5) break;
+        if (kg1 * h <= 32.0 && kg2 * h * h <= 0.25 && kg4 * h * h * h * h <= 1e-5) break;
     }
     if (logB < 6)
         return fail(ctx, BPS_ERR_UNSUPPORTED,

@@ -171,10 +171,13 @@ def plain_circular(n: int = 1 << 20, K: int = 32, seed: int = 1, with_series=Tru
     return w
 
 
-def htru_circular(n: int = 1 << 23, K: int = 4096, seed: int = 2, with_series=True) -> Workload:
+def htru_circular(n: int = 1 << 23, K: int = 4096, seed: int = 2, with_series=True,
+                  amp: float = 0.02) -> Workload:
     """HTRU-like: 2^23 samples at 64 us (537 s), N(0,1) + 3 pulsar-BH binaries
     (P U[20,100] ms, m_p 1.4, m_c 10 Msun, Porb U[3T,10T], cos i U[0,1),
-    tau = tau_max sin i); K-3 templates Porb U[3T,10T], tau U[0,3] lt-s, phi U."""
+    tau = tau_max sin i, peak amplitude 0.02 sigma: the single-pulse S/N of the
+    paper's simulations, Table 2); K-3 templates Porb U[3T,10T], tau U[0,3] lt-s,
+    phi U."""
     tsamp = 64e-6
     T = n * tsamp
     rng = np.random.default_rng(seed + 200)
@@ -184,7 +187,7 @@ def htru_circular(n: int = 1 << 23, K: int = 4096, seed: int = 2, with_series=Tr
         cosi = rng.uniform(0.0, 1.0)
         tau = float(tau_max(porb, 1.4, 10.0)) * math.sqrt(1.0 - cosi * cosi)
         pulsars.append(Pulsar(period_s=rng.uniform(0.020, 0.100), porb_s=porb,
-                              tau_lts=tau, phi_rad=rng.uniform(0.0, TWO_PI)))
+                              tau_lts=tau, phi_rad=rng.uniform(0.0, TWO_PI), amp=amp))
     bank, where = uniform_bank(K, seed + 100, (3 * T, 10 * T), (0.0, 3.0),
                                true_orbits=[p.orbit() for p in pulsars])
     w = Workload("HTRU-like circular search 2^%d x %d templates" % (int(math.log2(n)), K),
@@ -197,10 +200,11 @@ def htru_circular(n: int = 1 << 23, K: int = 4096, seed: int = 2, with_series=Tr
     return w
 
 
-def elliptical_imbh(n: int = 1 << 25, K: int = 2048, seed: int = 3, with_series=True) -> Workload:
+def elliptical_imbh(n: int = 1 << 25, K: int = 2048, seed: int = 3, with_series=True,
+                    amp: float = 0.02) -> Workload:
     """Elliptical IMBH-in-globular-cluster: 2^25 samples at 128 us, 2 pulsars with
-    e = 0.05 and 0.09 (P U[20,40] ms); K-2 templates Porb U[5T,10T], tau U[0,20],
-    phi, omega U[0,2pi), e U[0,0.1]."""
+    e = 0.05 and 0.09 (P U[20,40] ms, peak amplitude 0.02 sigma as in Table 2);
+    K-2 templates Porb U[5T,10T], tau U[0,20], phi, omega U[0,2pi), e U[0,0.1]."""
     tsamp = 128e-6
     T = n * tsamp
     rng = np.random.default_rng(seed + 200)
@@ -210,7 +214,7 @@ def elliptical_imbh(n: int = 1 << 25, K: int = 2048, seed: int = 3, with_series=
                               porb_s=rng.uniform(5 * T, 10 * T),
                               tau_lts=rng.uniform(0.0, 20.0),
                               phi_rad=rng.uniform(0.0, TWO_PI),
-                              omega_rad=rng.uniform(0.0, TWO_PI), ecc=e))
+                              omega_rad=rng.uniform(0.0, TWO_PI), ecc=e, amp=amp))
     bank, where = uniform_bank(K, seed + 100, (5 * T, 10 * T), (0.0, 20.0),
                                ecc=(0.0, 0.1), true_orbits=[p.orbit() for p in pulsars])
     w = Workload("elliptical IMBH search 2^%d x %d templates" % (int(math.log2(n)), K),

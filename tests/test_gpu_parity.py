@@ -8,7 +8,8 @@ import numpy as np
 import pytest
 
 import synth
-from gpu_common import PW_TOL, compare_candidates, pw_close, s_close
+from gpu_common import (PW_TOL, compare_candidates, oracle_on_gpu_maps, pw_close, s_close,
+                        validated_gpu_map)
 
 pytestmark = pytest.mark.gpu
 
@@ -53,15 +54,10 @@ def test_index_map_bitexact(bps, ctx, orc, logn, ts):
     x = synth.noise(n, 3)
     sid = ctx.load_series(x, ts)
     bid = ctx.load_bank(np.array(ORBITS))
-    total_near = 0
     for t, tm in enumerate(ORBITS):
-        gi, npre = ctx.index_map(sid, bid, t, n)
-        oi, off, near = orc.index_map(tm, n, ts)
-        bad = gi.astype(np.int64) != oi
-        assert not np.any(bad & ~near), (t, np.flatnonzero(bad & ~near)[:10])
-        total_near += int(near.sum())
+        gi, nd = validated_gpu_map(ctx, orc, sid, bid, t, tm, n, ts)
         if tm[1] == 0.0:
-            assert np.array_equal(gi, np.arange(n)) and npre == 0
+            assert np.array_equal(gi, np.arange(n)) and nd == 0
     ctx.unload(sid)
     ctx.unload(bid)
 
@@ -79,9 +75,10 @@ def test_whitened_spectrum_parity(bps, ctx, orc, logn, mode):
     W = min(1024, n // 2)
     prm = bps.default_params(whiten_block=W, mode=mode)
     pw = ctx.whitened_spectrum(sid, bid, 0, len(tms), n, prm)
-    for t, tm in enumerate(tms):
-        r = orc.search_template(x, ts, tm, whiten_block=W, want_arrays=True)
-        assert pw_close(pw[t], r["Pw"]) <= PW_TOL, (t, pw_close(pw[t], r["Pw"]))
+    _, res = oracle_on_gpu_maps(ctx, orc, sid, bid, x, ts, np.array(tms), want_arrays=True,
+                                whiten_block=W)
+    for t in range(len(tms)):
+        assert pw_close(pw[t], res[t]["Pw"]) <= PW_TOL, (t, pw_close(pw[t], res[t]["Pw"]))
     ctx.unload(sid)
     ctx.unload(bid)
 
@@ -95,7 +92,9 @@ def test_harmonic_sums_parity(bps, ctx, orc, w1, nharm):
     bid = ctx.load_bank(np.array([tm]))
     prm = bps.default_params(nharm_max=nharm)
     S = ctx.harmonic_sums(sid, bid, 0, n, prm)
-    r = orc.search_template(x, w1.tsamp, tm, nharm_max=nharm, want_arrays=True)
+    _, res = oracle_on_gpu_maps(ctx, orc, sid, bid, x, w1.tsamp, np.array([tm]), want_arrays=True,
+                                nharm_max=nharm)
+    r = res[0]
     for L in range(S.shape[0]):
         assert s_close(S[L], r["S"][L], 1 << L) <= PW_TOL, (L, s_close(S[L], r["S"][L], 1 << L))
     ctx.unload(sid)
@@ -112,7 +111,7 @@ def test_search_candidates_workload_2p20(bps, ctx, orc, w1, mode):
     rid = ctx.search(sid, bid, prm)
     gc, total = ctx.fetch_candidates(rid)
     assert total == gc.size
-    oc, counts, _ = orc.search(w1.series, w1.tsamp, w1.bank, cap_per=1 << 14)
+    oc, _ = oracle_on_gpu_maps(ctx, orc, sid, bid, w1.series, w1.tsamp, w1.bank)
     thr = bps.thresholds(prm, w1.n, w1.bank.shape[0])
     matched, excused = compare_candidates(gc, oc, thr)
     assert matched > 1000
@@ -158,7 +157,8 @@ def test_variants_parity(bps, ctx, orc, W, nharm, sigma):
     bid = ctx.load_bank(bank)
     prm = bps.default_params(whiten_block=W, nharm_max=nharm, sigma_thr=sigma)
     gc, _ = ctx.fetch_candidates(ctx.search(sid, bid, prm))
-    oc, _, _ = orc.search(x, ts, bank, nharm_max=nharm, whiten_block=W, sigma=sigma, cap_per=1 << 15)
+    oc, _ = oracle_on_gpu_maps(ctx, orc, sid, bid, x, ts, bank, nharm_max=nharm, whiten_block=W,
+                               sigma=sigma)
     compare_candidates(gc, oc, bps.thresholds(prm, n, 3))
     ctx.unload(sid)
     ctx.unload(bid)
@@ -173,12 +173,13 @@ def test_minimum_size(bps, ctx, orc):
     bid = ctx.load_bank(bank)
     prm = bps.default_params(whiten_block=32, sigma_thr=4.0)
     gc, _ = ctx.fetch_candidates(ctx.search(sid, bid, prm))
-    oc, _, _ = orc.search(x, ts, bank, whiten_block=32, sigma=4.0)
+    oc, res = oracle_on_gpu_maps(ctx, orc, sid, bid, x, ts, bank, want_arrays=True,
+                                 whiten_block=32, sigma=4.0)
     m, _ = compare_candidates(gc, oc, bps.thresholds(prm, n, 2))
     assert m > 0
     pw = ctx.whitened_spectrum(sid, bid, 0, 2, n, prm)
-    r = orc.search_template(x, ts, bank[0], whiten_block=32, want_arrays=True)
-    assert pw_close(pw[0], r["Pw"]) <= PW_TOL
+    for t in range(2):
+        assert pw_close(pw[t], res[t]["Pw"]) <= PW_TOL
 
 
 def test_zero_series_has_no_candidates(bps, ctx):
