@@ -199,6 +199,35 @@ int bps_set_profiling(bps_ctx* ctx, int on);
  * when profiling was on when the request was enqueued. */
 int bps_request_stats(bps_ctx* ctx, int64_t req_id, bps_stats* out);
 
+/* ---- allocation-free entry point -------------------------------------------- */
+
+/* The paper has no counterpart to this call: it serves callers that must not
+ * allocate device memory while they run -- e.g. real-time back ends that
+ * reserve all GPU memory at start-up, or host frameworks whose own pool
+ * allocator owns the device memory.  It computes the same whitened spectrum as
+ * bps_whitened_spectrum for ONE template, with the same kernels, but needs no
+ * context and calls no cudaMalloc, cudaFree or allocating library routine: its
+ * scratch is one fixed 8 MiB device array inside the library (held on every
+ * GPU that loads the library until the process exits).
+ *   d_series     n float32 samples in device memory of the current device
+ *   n            power of two in [2^11, 2^20]; larger n -> BPS_ERR_UNSUPPORTED
+ *   tsamp_s      sampling time [s], > 0
+ *   fill         value of samples mapped outside the series (the series mean)
+ *   tmpl         host pointer to one template (read during the call)
+ *   whiten_block power of two in [32, min(8192, n/2)]
+ *   d_pw_out     device buffer of n/2 floats receiving Pw_k, k in [0, n/2)
+ *   cuda_stream  cudaStream_t to run on (NULL = legacy default stream)
+ * Returns BPS_OK, BPS_ERR_INVALID_ARG, BPS_ERR_UNSUPPORTED or BPS_ERR_CUDA;
+ * the work is enqueued on the stream and the call does not wait for it.
+ * The scratch array is shared by every call and keeps the last call's
+ * contents; calls that overlap on the GPU race on it and must be serialised.
+ * The first call on a device looks up the array's address (cudaGetSymbolAddress,
+ * with that device current); make that first call before any stream capture. */
+int bps_whitened_spectrum_noalloc(const float* d_series, int64_t n, double tsamp_s,
+                                  double fill, const bps_template* tmpl,
+                                  int32_t whiten_block, float* d_pw_out,
+                                  void* cuda_stream);
+
 /* Per-level thresholds thr_n (n = 1, 2, ..., nharm_max) the search will use for
  * these parameters and problem size (host FP64). */
 int bps_thresholds(const bps_search_params* params, int64_t n_samples,

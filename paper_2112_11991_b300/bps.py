@@ -37,7 +37,7 @@ EXPORTED = ["bps_default_params", "bps_create", "bps_destroy", "bps_load_series"
             "bps_load_bank", "bps_search", "bps_query", "bps_fetch_candidates",
             "bps_unload", "bps_last_error", "bps_index_map", "bps_whitened_spectrum",
             "bps_harmonic_sums", "bps_thresholds", "bps_set_profiling",
-            "bps_request_stats"]
+            "bps_request_stats", "bps_whitened_spectrum_noalloc"]
 STAGES = ["anchors", "pass1", "pass2", "power", "median", "harmsum"]
 
 
@@ -116,6 +116,9 @@ def lib():
         L.bps_set_profiling.argtypes = [vp, i32]
         L.bps_request_stats.restype = i32
         L.bps_request_stats.argtypes = [vp, i64, P(bps_stats)]
+        L.bps_whitened_spectrum_noalloc.restype = i32
+        L.bps_whitened_spectrum_noalloc.argtypes = [vp, i64, C.c_double, C.c_double,
+                                                    P(bps_template), i32, vp, vp]
         L.bps_thresholds.restype = i32
         L.bps_thresholds.argtypes = [P(bps_search_params), i64, i64, vp]
         _lib = L
@@ -346,6 +349,12 @@ def bps_harmonic_sums(ctx, sid, bid, t, params, out):
 
 def bps_thresholds(params, n, k, out):
     return lib().bps_thresholds(params, n, k, out)
+
+
+def bps_whitened_spectrum_noalloc(d_series, n, tsamp, fill, tmpl, whiten_block, d_out, stream):
+    """Allocation-free whitened spectrum of one template (see include/bps.h)."""
+    return lib().bps_whitened_spectrum_noalloc(d_series, n, tsamp, fill, tmpl, whiten_block,
+                                               d_out, stream)
 
 
 def bps_set_profiling(ctx, on):
