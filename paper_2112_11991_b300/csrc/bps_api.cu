@@ -171,10 +171,7 @@ void thresholds(const bps_search_params* pr, int64_t n, int64_t K, double* out)
     for (int L = 0; L < nlev; ++L) out[L] = solve_threshold(1 << L, p);
 }
 
-// Geometry + anchor block length.  The anchor block B is the largest power of two
-// (<= 8192) for which, for every template, the FP32 fast path stays well inside its
-// 1e-4 guard: |inc| <= 32 samples, quadratic term <= 0.25 sample, quartic
-// remainder <= 1e-5 sample (h = B/2 the largest distance to the anchor centre).
+// Geometry (plan_geometry) + anchor block length (plan_anchor_block).
 int make_plan(bps_ctx* ctx, const Series& s, const Bank& b, const bps_search_params& pr,
               Plan& p)
 {
@@ -182,9 +179,7 @@ int make_plan(bps_ctx* ctx, const Series& s, const Bank& b, const bps_search_par
     p.logn = ilog2(s.n);
     p.M = s.n / 2;
     p.logM = p.logn - 1;
-    p.logR = p.logM / 2;
-    p.logC = p.logM - p.logR;
-    p.logG = std::min(p.logC, 14 - p.logR);
+    plan_geometry(p);
     p.logW = ilog2(pr.whiten_block);
     p.nharm = pr.nharm_max;
     p.lognh = ilog2(pr.nharm_max);
@@ -201,11 +196,7 @@ int make_plan(bps_ctx* ctx, const Series& s, const Bank& b, const bps_search_par
         Kmax = std::max(Kmax, K);
         gmax = std::max(gmax, K > 0 ? g : 0.0);
     }
-    int logB = std::min(13, p.logn);
-    for (; logB >= 6; --logB) {
-        const double h = (double)(1 << (logB - 1));
-        if (kg1 * h <= 32.0 && kg2 * h * h <= 0.25 && kg4 * h * h * h * h <= 1e-5) break;
-    }
+    const int logB = plan_anchor_block(kg1, kg2, kg4, p.logn);
     if (logB < 6)
         return fail(ctx, BPS_ERR_UNSUPPORTED,
                     "orbit too fast for the FP32 index map (tau/t_s = %.3g, Omega t_s/(1-e) = %.3g)",

@@ -42,6 +42,7 @@ struct Plan {
     int logn, logM;
     int logR, logC; // M = R * C (four-step: R-point column FFTs, C-point row FFTs)
     int logG;       // columns per CTA in pass 1
+    int logNP;      // row pairs per CTA in pass 2
     int logB;       // anchor block length B (samples)
     int64_t nanchor;// N / B
     int logW;       // whitening block W (bins)
@@ -50,6 +51,38 @@ struct Plan {
     int nlev;       // log2(nharm) + 1
     double tsamp;
 };
+
+// Four-step split of the packed FFT, M = R * C (both passes hold a tile of at most
+// 2^14 complex values in shared memory): C = 2^min(10, logM - 5) row length (pass 2),
+// R <= 2^13 column length (pass 1), G = 2^14 / R adjacent columns per pass-1 CTA,
+// NP = 2^13 / C row pairs per pass-2 CTA.
+inline void plan_geometry(Plan& p)
+{
+    p.logC = p.logM - 5 < 10 ? p.logM - 5 : 10;
+    p.logR = p.logM - p.logC;
+    if (p.logR > 13) {
+        p.logR = 13;
+        p.logC = p.logM - 13;
+    }
+    p.logG = p.logC < 14 - p.logR ? p.logC : 14 - p.logR;
+    p.logNP = (13 - p.logC) < (p.logR - 1) ? (13 - p.logC) : (p.logR - 1);
+}
+
+// Anchor block length B = 2^logB: the largest (<= 2^14, <= n) for which every
+// template keeps the FP32 fast path of the index map far inside its 1e-4 guard:
+// |linear increment| <= 128 samples, quadratic term <= 0.25 sample, quartic
+// remainder <= 1e-5 sample, with h = B/2 the largest distance to the anchor centre.
+// kg1, kg2, kg4 are the bank maxima of K g, K g^2, K g^4 (K = tau / t_s,
+// g = Omega t_s / (1 - e)).  Returns -1 when even B = 64 does not qualify.
+inline int plan_anchor_block(double kg1, double kg2, double kg4, int logn)
+{
+    int logB = logn < 14 ? logn : 14;
+    for (; logB >= 6; --logB) {
+        const double h = (double)(1 << (logB - 1));
+        if (kg1 * h <= 128.0 && kg2 * h * h <= 0.25 && kg4 * h * h * h * h <= 1e-5) return logB;
+    }
+    return -1;
+}
 
 // Thresholds of the harmonic levels, by value.
 struct Thr {

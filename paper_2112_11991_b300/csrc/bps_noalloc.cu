@@ -97,9 +97,7 @@ extern "C" int bps_whitened_spectrum_noalloc(const float* d_series, int64_t n, d
     p.logn = logn;
     p.M = n / 2;
     p.logM = logn - 1;
-    p.logR = p.logM / 2;
-    p.logC = p.logM - p.logR;
-    p.logG = p.logC < 14 - p.logR ? p.logC : 14 - p.logR;
+    plan_geometry(p);
     p.logW = logW;
     p.nharm = 1;
     p.lognh = 0;
@@ -107,12 +105,7 @@ extern "C" int bps_whitened_spectrum_noalloc(const float* d_series, int64_t n, d
     p.tsamp = tsamp_s;
     const double K = t.tau_lts / tsamp_s;
     const double g = (2.0 * M_PI / t.porb_s) * tsamp_s / (1.0 - t.ecc);
-    int logB = logn < 13 ? logn : 13;
-    for (; logB >= 6; --logB) {
-        const double h = (double)(1 << (logB - 1));
-        const double gh = g * h;
-        if (K * gh <= 32.0 && K * gh * gh <= 0.25 && K * gh * gh * gh * gh <= 1e-5) break;
-    }
+    const int logB = plan_anchor_block(K * g, K * g * g, K * g * g * g * g, logn);
     if (logB < 6) return BPS_ERR_UNSUPPORTED;
     p.logB = logB;
     p.nanchor = n >> logB;

@@ -7,9 +7,14 @@
 //   pass 1 (gather fused):  Y[k1][j2] = W_M^{j2 k1} * sum_{j1} z[j1 C + j2] W_R^{j1 k1}
 //   pass 2 (split + power fused):  Z[k1 + R k2] = sum_{j2} Y[k1][j2] W_C^{j2 k2}
 // then X_k = E_k + W_N^k O_k with E/O the even/odd-sample spectra recovered from
-// Z_k and Z_{M-k}; a pass-2 CTA owns the row pair (k1, R-k1) so both are local.
-// Each pass runs radix-4 (+ radix-2) Stockham stages in shared memory, one
-// sub-transform element set per thread held in registers across the barrier.
+// Z_k and Z_{M-k}.  A pass-2 CTA owns NP consecutive rows k1 and their mirrors
+// R - k1, so both halves of every split pair are local and the power of NP
+// consecutive bins is written as one run.
+//
+// Both passes hold a tile of at most 2^14 complex values in shared memory (padded
+// by one element per 16 against bank conflicts) and run radix-4 (+ radix-2)
+// Stockham stages; each thread keeps its EPT = 32 elements in registers across
+// the barrier between the read and the write of a stage.
 #include <cmath>
 
 #include "bps_internal.cuh"
@@ -18,6 +23,11 @@
 namespace bps {
 
 namespace {
+
+constexpr int kEPT = 32;
+constexpr int kLogTile = 14;  // largest tile (complex values per CTA) of both passes
+
+__device__ __forceinline__ int pad(int i) { return i + (i >> 4); }
 
 __device__ __forceinline__ float2 cmul(float2 a, float2 b)
 {
@@ -48,16 +58,16 @@ __device__ __forceinline__ void dft<4>(float2* v)
     v[3] = make_float2(a1.x - a3.y, a1.y + a3.x);  // a1 + i a3
 }
 
-// One Stockham stage over nlines lines of length L = 2^logL held in shared memory
-// (element (line, pos) at buf[line*ls + pos*es]).  Ns = 2^logNs is the length of
-// the sub-transforms already done.  blockDim.x * EPT == nlines * L.
+// One Stockham stage over 2^lognl lines of length L = 2^logL in shared memory;
+// element (line, pos) lives at buf[pad(line*ls + pos*es)].  Ns = 2^logNs is the
+// length of the sub-transforms already done.  blockDim.x * EPT == lines * L.
 template <int LOGRADIX, int EPT, bool LINE_FAST>
 __device__ __forceinline__ void fft_stage(float2* buf, int logL, int logNs, int lognl,
                                           int ls, int es, const float2* __restrict__ tw)
 {
     constexpr int RADIX = 1 << LOGRADIX;
     constexpr int BPT = EPT / RADIX;
-    const int logQ = logL - LOGRADIX;  // log2(L / RADIX)
+    const int logQ = logL - LOGRADIX;
     const int Q = 1 << logQ;
     const int Ns = 1 << logNs;
     const int twshift = 12 - logNs - LOGRADIX;  // 4096 / (Ns * RADIX)
@@ -78,7 +88,7 @@ __device__ __forceinline__ void fft_stage(float2* buf, int logL, int logNs, int 
         const int base = line * ls;
 #pragma unroll
         for (int s = 0; s < RADIX; ++s) {
-            float2 x = buf[base + (j + s * Q) * es];
+            float2 x = buf[pad(base + (j + s * Q) * es)];
             if (s > 0) x = cmul(x, __ldg(tw + ((k * s) << twshift)));
             v[i * RADIX + s] = x;
         }
@@ -89,7 +99,7 @@ __device__ __forceinline__ void fft_stage(float2* buf, int logL, int logNs, int 
     for (int i = 0; i < BPT; ++i) {
         dft<RADIX>(v + i * RADIX);
 #pragma unroll
-        for (int s = 0; s < RADIX; ++s) buf[dst[i] + s * Ns * es] = v[i * RADIX + s];
+        for (int s = 0; s < RADIX; ++s) buf[pad(dst[i] + s * Ns * es)] = v[i * RADIX + s];
     }
     __syncthreads();
 }
@@ -104,8 +114,6 @@ __device__ __forceinline__ void smem_fft(float2* buf, int logL, int lognl, int l
     if (logNs < logL) fft_stage<1, EPT, LINE_FAST>(buf, logL, logNs, lognl, ls, es, tw);
 }
 
-constexpr int kEPT = 32;
-
 __global__ void k_twiddle_init(float2* tw)
 {
     const int t = blockIdx.x * blockDim.x + threadIdx.x;
@@ -116,106 +124,182 @@ __global__ void k_twiddle_init(float2* tw)
     }
 }
 
+// e^{-2 pi i t / 2^logD} for an exact integer t < 2^24
+__device__ __forceinline__ float2 twiddle(uint32_t t, int logD)
+{
+    float s, c;
+    sincospif(ldexpf((float)t, 1 - logD), &s, &c);
+    return make_float2(c, -s);
+}
+
 // Pass 1: index map + gather of 2G consecutive samples per row, R-point column
 // FFTs over j1 for G adjacent columns, four-step twiddle, coalesced store.
-__global__ void __launch_bounds__(512) k_pass1(SeriesView x, const Anchor* __restrict__ anc,
-                                               Plan p, const float2* __restrict__ tw,
-                                               float2* __restrict__ Y)
+// Each thread first evaluates the index map of a chunk of its samples (anchor
+// loads and arithmetic, independent), fixes the rare near-boundary ones with the
+// compensated evaluation, then issues all the chunk's gathers before storing them.
+__global__ void __launch_bounds__(512, 1) k_pass1(SeriesView x, const Anchor* __restrict__ anc,
+                                                  Plan p, const float2* __restrict__ tw,
+                                                  float2* __restrict__ Y)
 {
     extern __shared__ float2 sm[];
     const int tl = blockIdx.y;
-    const int G = 1 << p.logG;
-    const int nel = 1 << (p.logR + p.logG);
-    const int c0 = blockIdx.x << p.logG;
+    const int logG = p.logG;
+    const int G = 1 << logG;
+    const int nthr = blockDim.x;
+    const int c0 = blockIdx.x << logG;
     const Anchor* at = anc + (int64_t)tl * p.nanchor;
-    for (int e = threadIdx.x; e < nel; e += blockDim.x) {
-        const int j1 = e >> p.logG, g = e & (G - 1);
-        const int64_t m = 2 * (((int64_t)j1 << p.logC) + c0 + g);
-        const int64_t b = anchor_of(m, p.logB);
-        const Anchor a = at[b];
-        const int d = (int)(m - anchor_centre(b, p.logB));
-        bool pr;
-        const int k0 = off_round(a, d, pr);
-        const int k1 = off_round(a, d + 1, pr);
-        const float v0 = gather_sample(x, p.n, m + a.I + k0);
-        const float v1 = gather_sample(x, p.n, m + 1 + a.I + k1);
-        sm[e] = make_float2(v0, v1);
+    constexpr int CH = 8;  // elements per gather chunk (16 samples)
+#pragma unroll
+    for (int c = 0; c < kEPT; c += CH) {
+        int id[2 * CH];
+        unsigned pm = 0;
+#pragma unroll
+        for (int i = 0; i < CH; ++i) {
+            const int e = threadIdx.x + (c + i) * nthr;
+            const int j1 = e >> logG, g = e & (G - 1);
+            const int m = 2 * ((j1 << p.logC) + c0 + g);
+            const int b = m >> p.logB;
+            const float4 a4 = __ldg(reinterpret_cast<const float4*>(at + b));
+            const float q3 = __ldg(&at[b].q3);
+            const int I = __float_as_int(a4.x);
+            const float fh = a4.y + 0.5f, L = a4.z, q2 = a4.w;
+            const int d = m - ((b << p.logB) + (1 << (p.logB - 1)));
+#pragma unroll
+            for (int u = 0; u < 2; ++u) {
+                const float df = (float)(d + u);
+                const float xx = fh - df * fmaf(df, fmaf(df, q3, q2), L);
+                const float fl = floorf(xx);
+                const float fr = xx - fl;
+                if (!(fr > kGuard && fr < 1.f - kGuard)) pm |= 1u << (2 * i + u);
+                id[2 * i + u] = m + u + I + (int)fl;
+            }
+        }
+        if (pm) {
+#pragma unroll
+            for (int i = 0; i < CH; ++i) {
+#pragma unroll
+                for (int u = 0; u < 2; ++u) {
+                    if (pm & (1u << (2 * i + u))) {
+                        const int e = threadIdx.x + (c + i) * nthr;
+                        const int j1 = e >> logG, g = e & (G - 1);
+                        const int m = 2 * ((j1 << p.logC) + c0 + g);
+                        const int b = m >> p.logB;
+                        const Anchor a = at[b];
+                        const int d = m - ((b << p.logB) + (1 << (p.logB - 1)));
+                        id[2 * i + u] = m + u + a.I + off_round_precise(a, d + u);
+                    }
+                }
+            }
+        }
+        float v[2 * CH];
+#pragma unroll
+        for (int q = 0; q < 2 * CH; ++q) v[q] = gather_sample(x, p.n, id[q]);
+#pragma unroll
+        for (int i = 0; i < CH; ++i) {
+            const int e = threadIdx.x + (c + i) * nthr;
+            sm[pad(e)] = make_float2(v[2 * i], v[2 * i + 1]);
+        }
     }
     __syncthreads();
-    smem_fft<kEPT, true>(sm, p.logR, p.logG, 1, G, tw);
+    smem_fft<kEPT, true>(sm, p.logR, logG, 1, G, tw);
+    // four-step twiddle W_M^{j2 k1}: j2 is fixed per thread, k1 steps by nthr/G
+    const int g = threadIdx.x & (G - 1);
+    const uint32_t j2 = (uint32_t)(c0 + g);
+    const uint32_t k10 = (uint32_t)(threadIdx.x >> logG);
+    const uint32_t dk = (uint32_t)(nthr >> logG);
+    const uint32_t Mm = (uint32_t)(p.M - 1);
+    float2 w = twiddle((j2 * k10) & Mm, p.logM);
+    const float2 st = twiddle((j2 * dk) & Mm, p.logM);
     float2* Yt = Y + (int64_t)tl * p.M;
-    for (int e = threadIdx.x; e < nel; e += blockDim.x) {
-        const int k1 = e >> p.logG, g = e & (G - 1);
-        const int j2 = c0 + g;
-        const uint32_t t = ((uint32_t)j2 * (uint32_t)k1) & (uint32_t)(p.M - 1);
-        float s, c;
-        sincospif(ldexpf((float)t, 1 - p.logM), &s, &c);
-        Yt[((int64_t)k1 << p.logC) + j2] = cmul(sm[e], make_float2(c, -s));
+#pragma unroll 8
+    for (int i = 0; i < kEPT; ++i) {
+        const int e = threadIdx.x + i * nthr;
+        const int k1 = e >> logG;
+        Yt[((int64_t)k1 << p.logC) + j2] = cmul(sm[pad(e)], w);
+        w = cmul(w, st);
     }
 }
 
-// |X_k|^2 and |X_{M-k}|^2 from Z_k, Z_{M-k}:  E = (Z_k + conj Z_{M-k})/2,
-// O = -i (Z_k - conj Z_{M-k})/2,  X_k = E + W_N^k O,  X_{M-k} = conj(E - W_N^k O).
-__device__ __forceinline__ void power_pair(float2 zk, float2 zm, int64_t k, int logn,
-                                           float& pa, float& pb)
+// |X_k|^2 and |X_{M-k}|^2 from Z_k, Z_{M-k} and w = W_N^k:
+// E = (Z_k + conj Z_{M-k})/2, O = -i (Z_k - conj Z_{M-k})/2,
+// X_k = E + w O,  X_{M-k} = conj(E - w O).
+__device__ __forceinline__ void power_pair(float2 zk, float2 zm, float2 w, float& pa, float& pb)
 {
     const float2 E = make_float2(0.5f * (zk.x + zm.x), 0.5f * (zk.y - zm.y));
     const float2 O = make_float2(0.5f * (zk.y + zm.y), -0.5f * (zk.x - zm.x));
-    float s, c;
-    sincospif(ldexpf((float)k, 1 - logn), &s, &c);
-    const float2 t = cmul(make_float2(c, -s), O);
+    const float2 t = cmul(w, O);
     const float ar = E.x + t.x, ai = E.y + t.y;
     const float br = E.x - t.x, bi = E.y - t.y;
     pa = ar * ar + ai * ai;
     pb = br * br + bi * bi;
 }
 
-// Pass 2: C-point FFTs of the row pair (k1, R - k1) (pair 0 holds the self-
-// mirrored rows 0 and R/2), real-FFT split and power, written in natural bin order.
-__global__ void __launch_bounds__(512) k_pass2(const float2* __restrict__ Y, Plan p,
-                                               const float2* __restrict__ tw,
-                                               float* __restrict__ P)
+// Pass 2: C-point FFTs of NP row pairs (q, R - q), q in [q0, q0 + NP) (pair 0 holds
+// the self-mirrored rows 0 and R/2), then real-FFT split and power.  Items are
+// assigned q-fastest so each warp writes NP consecutive bins per k2.
+__global__ void __launch_bounds__(512, 1) k_pass2(const float2* __restrict__ Y, Plan p,
+                                                  const float2* __restrict__ tw,
+                                                  float* __restrict__ P)
 {
     extern __shared__ float2 sm[];
     const int tl = blockIdx.y;
-    const int R = 1 << p.logR, C = 1 << p.logC;
-    const int pr = blockIdx.x;
-    const int rowA = pr, rowB = (pr == 0) ? (R >> 1) : (R - pr);
+    const int logR = p.logR, logC = p.logC;
+    const int R = 1 << logR, C = 1 << logC;
+    const int logNP = p.logNP;
+    const int NP = 1 << logNP;
+    const int q0 = blockIdx.x << logNP;
+    const int nthr = blockDim.x;
     const float2* Yt = Y + (int64_t)tl * p.M;
-    for (int e = threadIdx.x; e < 2 * C; e += blockDim.x) {
-        const int line = e >> p.logC, j2 = e & (C - 1);
-        const int row = line ? rowB : rowA;
-        sm[e] = Yt[((int64_t)row << p.logC) + j2];
+    // lines [0, NP): low rows q0 + l ; lines [NP, 2NP): their mirrors
+#pragma unroll 8
+    for (int i = 0; i < kEPT; ++i) {
+        const int e = threadIdx.x + i * nthr;
+        const int line = e >> logC, j2 = e & (C - 1);
+        const int q = q0 + (line & (NP - 1));
+        const int row = (line < NP) ? q : (q == 0 ? (R >> 1) : R - q);
+        sm[pad(e)] = __ldg(Yt + ((int64_t)row << logC) + j2);
     }
     __syncthreads();
-    smem_fft<kEPT, false>(sm, p.logC, 1, C, 1, tw);
+    smem_fft<kEPT, false>(sm, logC, logNP + 1, C, 1, tw);
     float* Pt = P + (int64_t)tl * p.M;
-    if (pr != 0) {
-        for (int k2 = threadIdx.x; k2 < C; k2 += blockDim.x) {
-            const int64_t k = rowA + ((int64_t)k2 << p.logR);
+    // W_N^{q + R k2} = W_N^q * W_{2C}^{k2};  W_{2C}^{k2} = tw[k2 * 4096 / (2C)]
+    const int ql = threadIdx.x & (NP - 1);
+    const int q = q0 + ql;
+    const float2 wq = twiddle((uint32_t)q, p.logn);
+    const int twsh = 11 - logC;
+    const int lowl = ql, highl = NP + ql;
+    const int items = NP * C;
+    for (int it = threadIdx.x; it < items; it += nthr) {
+        const int k2 = it >> logNP;
+        if (q != 0) {
+            const int64_t k = q + ((int64_t)k2 << logR);
+            const float2 w = cmul(wq, __ldg(tw + (k2 << twsh)));
             float pa, pb;
-            power_pair(sm[k2], sm[C + (C - 1 - k2)], k, p.logn, pa, pb);
+            power_pair(sm[pad(lowl * C + k2)], sm[pad(highl * C + (C - 1 - k2))], w, pa, pb);
             Pt[k] = pa;
             Pt[p.M - k] = pb;
-        }
-    } else {
-        for (int k2 = threadIdx.x; k2 <= (C >> 1); k2 += blockDim.x) {
-            const int64_t k = (int64_t)k2 << p.logR;
-            float pa, pb;
-            power_pair(sm[k2], sm[(C - k2) & (C - 1)], k, p.logn, pa, pb);
-            if (k2 == 0) {
-                Pt[0] = 0.f;
-            } else {
-                Pt[k] = pa;
-                if (k2 != (C >> 1)) Pt[p.M - k] = pb;
+        } else {
+            if (k2 <= (C >> 1)) {  // row 0: bins R k2 and M - R k2
+                const int64_t k = (int64_t)k2 << logR;
+                float pa, pb;
+                power_pair(sm[pad(k2)], sm[pad((C - k2) & (C - 1))], __ldg(tw + (k2 << twsh)),
+                           pa, pb);
+                if (k2 == 0) {
+                    Pt[0] = 0.f;
+                } else {
+                    Pt[k] = pa;
+                    if (k2 != (C >> 1)) Pt[p.M - k] = pb;
+                }
             }
-        }
-        for (int k2 = threadIdx.x; k2 < (C >> 1); k2 += blockDim.x) {
-            const int64_t k = (R >> 1) + ((int64_t)k2 << p.logR);
-            float pa, pb;
-            power_pair(sm[C + k2], sm[C + (C - 1 - k2)], k, p.logn, pa, pb);
-            Pt[k] = pa;
-            Pt[p.M - k] = pb;
+            if (k2 < (C >> 1)) {  // row R/2: bins R/2 + R k2 and M - (R/2 + R k2)
+                const int64_t k = (R >> 1) + ((int64_t)k2 << logR);
+                const float2 w =
+                    cmul(twiddle((uint32_t)(R >> 1), p.logn), __ldg(tw + (k2 << twsh)));
+                float pa, pb;
+                power_pair(sm[pad(highl * C + k2)], sm[pad(highl * C + (C - 1 - k2))], w, pa, pb);
+                Pt[k] = pa;
+                Pt[p.M - k] = pb;
+            }
         }
     }
 }
@@ -230,6 +314,8 @@ __global__ void k_power_r2c(const float2* __restrict__ X, Plan p, float* __restr
     P[(int64_t)tl * p.M + k] = (k == 0) ? 0.f : z.x * z.x + z.y * z.y;
 }
 
+size_t tile_smem(int logt) { return (size_t)(((1 << logt) + ((1 << logt) >> 4)) * sizeof(float2)); }
+
 }  // namespace
 
 cudaError_t launch_twiddle_init(float2* tw4096, cudaStream_t s)
@@ -241,32 +327,24 @@ cudaError_t launch_twiddle_init(float2* tw4096, cudaStream_t s)
 cudaError_t launch_pass1(const SeriesView& x, const Anchor* anc, int nt, const Plan& p,
                          const float2* tw, float2* Y, cudaStream_t s)
 {
-    const int nel = 1 << (p.logR + p.logG);
-    const int threads = nel / kEPT;
-    const size_t smem = (size_t)nel * sizeof(float2);
-    static bool attr = false;
-    if (!attr) {
-        cudaFuncSetAttribute(k_pass1, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024);
-        attr = true;
-    }
+    const int logt = p.logR + p.logG;
+    cudaError_t e = cudaFuncSetAttribute(k_pass1, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                         (int)tile_smem(kLogTile));
+    if (e != cudaSuccess) return e;
     dim3 grid((unsigned)(1 << (p.logC - p.logG)), (unsigned)nt);
-    k_pass1<<<grid, threads, smem, s>>>(x, anc, p, tw, Y);
+    k_pass1<<<grid, (1 << logt) / kEPT, tile_smem(logt), s>>>(x, anc, p, tw, Y);
     return cudaGetLastError();
 }
 
 cudaError_t launch_pass2(const float2* Y, int nt, const Plan& p, const float2* tw, float* P,
                          cudaStream_t s)
 {
-    const int nel = 2 << p.logC;
-    const int threads = nel / kEPT;
-    const size_t smem = (size_t)nel * sizeof(float2);
-    static bool attr = false;
-    if (!attr) {
-        cudaFuncSetAttribute(k_pass2, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024);
-        attr = true;
-    }
-    dim3 grid((unsigned)(1 << (p.logR - 1)), (unsigned)nt);
-    k_pass2<<<grid, threads, smem, s>>>(Y, p, tw, P);
+    const int logt = p.logNP + 1 + p.logC;
+    cudaError_t e = cudaFuncSetAttribute(k_pass2, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                         (int)tile_smem(kLogTile));
+    if (e != cudaSuccess) return e;
+    dim3 grid((unsigned)(1 << (p.logR - 1 - p.logNP)), (unsigned)nt);
+    k_pass2<<<grid, (1 << logt) / kEPT, tile_smem(logt), s>>>(Y, p, tw, P);
     return cudaGetLastError();
 }
 

@@ -7,7 +7,7 @@
 // equation by FP64 Newton iteration, evaluates the BT delay and the zero offset
 // t_0 = Delta_R(0)/t_s, and stores the FP32 constants the per-sample
 // evaluation (index_map.cuh) needs.  FP64 work is N/B Kepler solves per
-// template (B is chosen by the planner, typically 4096 samples).
+// template (B is chosen by the planner, typically 4096-16384 samples).
 #include <cmath>
 
 #include "bps_internal.cuh"
@@ -184,8 +184,8 @@ __global__ void k_f16_pack(const float* __restrict__ x, int64_t n, uint16_t* __r
 cudaError_t launch_anchors(const DevTemplate* bank, int64_t t0, int nt, const Plan& p,
                            Anchor* out, cudaStream_t s)
 {
-    dim3 grid((unsigned)((p.nanchor + 127) / 128), (unsigned)nt);
-    k_anchors<<<grid, 128, 0, s>>>(bank, t0, p, out);
+    dim3 grid((unsigned)((p.nanchor + 63) / 64), (unsigned)nt);
+    k_anchors<<<grid, 64, 0, s>>>(bank, t0, p, out);
     return cudaGetLastError();
 }
 
