@@ -251,7 +251,9 @@ def main():
     n = w.n
     K = bank.shape[0]
     ctx = bps.Context(local)
-    stream = torch.cuda.current_stream(dev)
+    # a real stream: the library runs on the stream it is given, and the CUDA events
+    # below are recorded on the same one
+    stream = torch.cuda.Stream(dev)
     sid = ctx.load_series(w.series, w.tsamp)
     bid = ctx.load_bank(bank)
     flush = torch.empty(256 << 20, dtype=torch.uint8, device=dev)

@@ -235,9 +235,14 @@ struct Workspace {
 
 size_t align256(size_t v) { return (v + 255) & ~(size_t)255; }
 
-int ws_alloc(bps_ctx* ctx, const Plan& p, int nt, int mode, cudaStream_t st, Workspace& w)
+// Anchors are computed for a chunk of up to kAnchorChunk batches in one launch.
+constexpr int kAnchorChunk = 8;
+
+int ws_alloc(bps_ctx* ctx, const Plan& p, int nt, int mode, cudaStream_t st, Workspace& w,
+             int anchor_templates = 0)
 {
-    const size_t a = align256(sizeof(Anchor) * (size_t)p.nanchor * nt);
+    const size_t a = align256(sizeof(Anchor) * (size_t)p.nanchor *
+                              (anchor_templates > 0 ? anchor_templates : nt));
     const size_t y = align256(sizeof(float2) * (size_t)(p.M + 1) * nt);
     const size_t x = mode == BPS_MODE_PLAIN ? align256(sizeof(float) * (size_t)p.n * nt) : 0;
     const size_t pp = align256(sizeof(float) * (size_t)p.M * nt);
@@ -297,15 +302,19 @@ struct StageTimer {
 // Runs the spectrum stages for templates [t0, t0+nt): anchors -> (fused) pass1/pass2
 // or (plain) resample/cuFFT/power -> block medians.  P and scale are left in w.
 int run_spectrum(bps_ctx* ctx, const Series& s, const Bank& b, const Plan& p, int mode,
-                 int64_t t0, int nt, Workspace& w, cudaStream_t st, StageTimer& tm)
+                 int64_t t0, int nt, Workspace& w, cudaStream_t st, StageTimer& tm,
+                 const Anchor* anc = nullptr)
 {
-    tm.begin(BPS_STAGE_ANCHORS);
-    CK(launch_anchors(b.d, t0, nt, p, w.anc, st));
-    tm.end();
+    if (!anc) {
+        tm.begin(BPS_STAGE_ANCHORS);
+        CK(launch_anchors(b.d, t0, nt, p, w.anc, st));
+        tm.end();
+        anc = w.anc;
+    }
     const SeriesView v = view_of(s);
     if (mode == BPS_MODE_FUSED) {
         tm.begin(BPS_STAGE_PASS1);
-        CK(launch_pass1(v, w.anc, nt, p, ctx->tw, w.Y, st));
+        CK(launch_pass1(v, anc, nt, p, ctx->tw, w.Y, st));
         tm.end();
         tm.begin(BPS_STAGE_PASS2);
         CK(launch_pass2(w.Y, nt, p, ctx->tw, w.P, st));
@@ -315,7 +324,7 @@ int run_spectrum(bps_ctx* ctx, const Series& s, const Bank& b, const Plan& p, in
         int rc = get_fft(ctx, p.n, nt, h);
         if (rc) return rc;
         tm.begin(BPS_STAGE_PASS1);
-        CK(launch_resample(v, w.anc, nt, p, w.x, st));
+        CK(launch_resample(v, anc, nt, p, w.x, st));
         tm.end();
         cufftSetStream(h, st);
         tm.begin(BPS_STAGE_PASS2);
@@ -372,7 +381,7 @@ int bps_create(bps_ctx** out, int device)
     ctx->device = device;
     if (cudaSetDevice(device) != cudaSuccess ||
         cudaStreamCreateWithFlags(&ctx->stream, cudaStreamNonBlocking) != cudaSuccess ||
-        cudaMalloc((void**)&ctx->tw, 4096 * sizeof(float2)) != cudaSuccess ||
+        cudaMalloc((void**)&ctx->tw, kTwiddleN * sizeof(float2)) != cudaSuccess ||
         launch_twiddle_init(ctx->tw, ctx->stream) != cudaSuccess ||
         cudaStreamSynchronize(ctx->stream) != cudaSuccess) {
         delete ctx;
@@ -539,8 +548,9 @@ int bps_search(bps_ctx* ctx, int64_t series_id, int64_t bank_id, const bps_searc
     CK(cudaEventCreateWithFlags(&r.done, cudaEventDisableTiming));
     const int nt = params->batch > 0 ? (int)std::min<int64_t>(params->batch, b->K)
                                      : default_batch(p, b->K, params->mode);
+    const int64_t chunk = std::min<int64_t>((int64_t)nt * kAnchorChunk, b->K);
     Workspace w;
-    if ((rc = ws_alloc(ctx, p, nt, params->mode, st, w))) {
+    if ((rc = ws_alloc(ctx, p, nt, params->mode, st, w, (int)chunk))) {
         free_request(r);
         return rc;
     }
@@ -550,16 +560,28 @@ int bps_search(bps_ctx* ctx, int64_t series_id, int64_t bank_id, const bps_searc
     tm.r = &r;
     tm.st = st;
     tm.prof = ctx->profiling;
-    for (int64_t t0 = 0; t0 < b->K; t0 += nt) {
-        const int cnt = (int)std::min<int64_t>(nt, b->K - t0);
-        if ((rc = run_spectrum(ctx, *s, *b, p, params->mode, t0, cnt, w, st, tm))) break;
-        tm.begin(BPS_STAGE_HARMSUM);
-        cudaError_t e = launch_harmsum(w.P, w.scale, cnt, t0, p, th, r.d_cands, r.cap, r.d_count,
-                                       nullptr, st);
+    for (int64_t c0 = 0; c0 < b->K && !rc; c0 += chunk) {
+        const int ccnt = (int)std::min<int64_t>(chunk, b->K - c0);
+        tm.begin(BPS_STAGE_ANCHORS);
+        cudaError_t e = launch_anchors(b->d, c0, ccnt, p, w.anc, st);
         tm.end();
         if (e != cudaSuccess) {
-            rc = fail(ctx, BPS_ERR_CUDA, "harmonic-sum launch: %s", cudaGetErrorString(e));
+            rc = fail(ctx, BPS_ERR_CUDA, "anchor launch: %s", cudaGetErrorString(e));
             break;
+        }
+        for (int64_t t0 = c0; t0 < c0 + ccnt; t0 += nt) {
+            const int cnt = (int)std::min<int64_t>(nt, c0 + ccnt - t0);
+            if ((rc = run_spectrum(ctx, *s, *b, p, params->mode, t0, cnt, w, st, tm,
+                                   w.anc + (t0 - c0) * p.nanchor)))
+                break;
+            tm.begin(BPS_STAGE_HARMSUM);
+            e = launch_harmsum(w.P, w.scale, cnt, t0, p, th, r.d_cands, r.cap, r.d_count, nullptr,
+                               st);
+            tm.end();
+            if (e != cudaSuccess) {
+                rc = fail(ctx, BPS_ERR_CUDA, "harmonic-sum launch: %s", cudaGetErrorString(e));
+                break;
+            }
         }
     }
     cudaFreeAsync(w.base, st);

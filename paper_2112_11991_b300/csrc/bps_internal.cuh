@@ -107,7 +107,9 @@ struct SeriesView {
 };
 
 // Launchers (stream-ordered, return cudaGetLastError()).
-cudaError_t launch_twiddle_init(float2* tw4096, cudaStream_t s);
+// tw[t] = exp(-2 pi i t / kTwiddleN), t in [0, kTwiddleN): covers every FFT length <= 8192
+constexpr int kTwiddleN = 8192;
+cudaError_t launch_twiddle_init(float2* tw, cudaStream_t s);
 cudaError_t launch_anchors(const DevTemplate* bank, int64_t t0, int nt, const Plan& p,
                            Anchor* out, cudaStream_t s);
 cudaError_t launch_index_map(const Anchor* anc, const Plan& p, int32_t* idx,
@@ -120,10 +122,13 @@ cudaError_t launch_pass2(const float2* Y, int nt, const Plan& p, const float2* t
                          float* P, cudaStream_t s);
 cudaError_t launch_power_from_r2c(const float2* X, int nt, const Plan& p, float* P,
                                   cudaStream_t s);
-cudaError_t launch_block_median(const float* P, int nt, const Plan& p, float* scale,
+// finds the block medians and whitens P in place (P -> Pw); scale receives ln2/med
+cudaError_t launch_block_median(float* P, int nt, const Plan& p, float* scale,
                                 cudaStream_t s);
+// copies the whitened spectrum left by launch_block_median (scale unused)
 cudaError_t launch_whitened(const float* P, const float* scale, int nt, const Plan& p,
                             float* out, cudaStream_t s);
+// P holds the whitened spectrum (after launch_block_median); scale unused
 cudaError_t launch_harmsum(const float* P, const float* scale, int nt, int64_t tidx0,
                            const Plan& p, const Thr& thr, Cand* cands, int64_t cap,
                            unsigned long long* count, float* s_out, cudaStream_t s);

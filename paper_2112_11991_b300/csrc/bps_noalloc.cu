@@ -111,7 +111,7 @@ extern "C" int bps_whitened_spectrum_noalloc(const float* d_series, int64_t n, d
     p.nanchor = n >> logB;
 
     // carve the scratch array
-    const size_t a_tw = up256(4096 * sizeof(float2));
+    const size_t a_tw = up256(kTwiddleN * sizeof(float2));
     const size_t a_tm = up256(sizeof(DevTemplate));
     const size_t a_an = up256(sizeof(Anchor) * (size_t)p.nanchor);
     const size_t a_y = up256(sizeof(float2) * (size_t)(p.M + 1));

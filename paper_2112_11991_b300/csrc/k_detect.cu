@@ -2,8 +2,8 @@
 //
 // De-reddening (App. A, "Fourier de-reddening"): per block of W consecutive bins
 // the lower median med_b (the element of rank floor((W-1)/2)) is found by an exact
-// 4 x 8-bit radix select on the FP32 bit patterns (P >= 0, so bit order is value
-// order); the block scale ln2 / med_b makes white noise Exp(1).
+// radix select on the FP32 bit patterns (P >= 0, so bit order is value order) and
+// the block is whitened in place, Pw = P ln2 / med_b (white noise -> Exp(1)).
 //
 // Harmonic sum (Sec. 2.1, S_L = sum_{n <= 2^L} P_n): with H = nharm_max,
 // F_h = Pw[(k h + H/2) div H] for h = 1..H, and (k h' + n/2) div n equals
@@ -20,7 +20,7 @@ namespace {
 
 constexpr float kLn2 = 0.693147180559945309417f;
 
-__global__ void __launch_bounds__(256) k_block_median(const float* __restrict__ P, Plan p,
+__global__ void __launch_bounds__(256) k_block_median(float* __restrict__ P, Plan p,
                                                       float* __restrict__ scale)
 {
     extern __shared__ uint32_t sv[];
@@ -29,7 +29,7 @@ __global__ void __launch_bounds__(256) k_block_median(const float* __restrict__ 
     const int tl = blockIdx.y;
     const int64_t blk = blockIdx.x;
     const int W = 1 << p.logW;
-    const float* src = P + (int64_t)tl * p.M + (blk << p.logW);
+    float* src = P + (int64_t)tl * p.M + (blk << p.logW);
     for (int i = threadIdx.x; i < W; i += blockDim.x) sv[i] = __float_as_uint(src[i]);
     uint32_t prefix = 0, pmask = 0, rank = (uint32_t)(W - 1) / 2;
     for (int shift = 24; shift >= 0; shift -= 8) {
@@ -74,28 +74,27 @@ __global__ void __launch_bounds__(256) k_block_median(const float* __restrict__ 
         rank = s_rank;
         __syncthreads();
     }
-    if (threadIdx.x == 0) {
-        const float med = __uint_as_float(prefix);
-        scale[(int64_t)tl * (p.M >> p.logW) + blk] = (med > 0.f) ? kLn2 / med : 0.f;
-    }
+    const float med = __uint_as_float(prefix);
+    const float sc = (med > 0.f) ? kLn2 / med : 0.f;
+    for (int i = threadIdx.x; i < W; i += blockDim.x) src[i] = __uint_as_float(sv[i]) * sc;
+    if (threadIdx.x == 0) scale[(int64_t)tl * (p.M >> p.logW) + blk] = sc;
 }
 
-__global__ void k_whitened(const float* __restrict__ P, const float* __restrict__ scale, Plan p,
-                           float* __restrict__ out)
+__global__ void k_whitened(const float* __restrict__ Pw, Plan p, float* __restrict__ out)
 {
     const int tl = blockIdx.y;
     const int64_t k = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     if (k >= p.M) return;
-    out[(int64_t)tl * p.M + k] =
-        P[(int64_t)tl * p.M + k] * scale[(int64_t)tl * (p.M >> p.logW) + (k >> p.logW)];
+    out[(int64_t)tl * p.M + k] = Pw[(int64_t)tl * p.M + k];
 }
 
 // One warp per block of W = 32*VPL bins, values in registers; exact radix select of
-// the element of rank floor((W-1)/2) over 4 x 8-bit digits with a per-warp
-// histogram (equal digits of a warp aggregated by __match_any_sync, one shared
-// atomic per distinct digit) and a warp prefix scan.  No block-level barrier.
+// the element of rank floor((W-1)/2) over four digits of the FP32 bit pattern
+// (P >= 0: sign bit 0; digits = exponent [30:23], mantissa [22:15], [14:7], [6:0])
+// with a per-warp shared histogram and a warp prefix scan, no block barrier.  The
+// block is then whitened in place: Pw = P * ln2 / med (0 when med = 0).
 template <int VPL>
-__global__ void __launch_bounds__(256) k_median_warp(const float* __restrict__ P, Plan p,
+__global__ void __launch_bounds__(256) k_median_warp(float* __restrict__ P, Plan p,
                                                      float* __restrict__ scale)
 {
     __shared__ uint32_t hist[8][256];
@@ -104,24 +103,22 @@ __global__ void __launch_bounds__(256) k_median_warp(const float* __restrict__ P
     const int64_t nblk = p.M >> p.logW;
     const int64_t blk = (int64_t)blockIdx.x * 8 + warp;
     if (blk >= nblk) return;
-    const float* src = P + (int64_t)tl * p.M + (blk << p.logW);
+    float* src = P + (int64_t)tl * p.M + (blk << p.logW);
     uint32_t u[VPL];
 #pragma unroll
-    for (int i = 0; i < VPL; ++i) u[i] = __float_as_uint(__ldg(src + lane + 32 * i));
+    for (int i = 0; i < VPL; ++i) u[i] = __float_as_uint(src[lane + 32 * i]);
     uint32_t prefix = 0, pmask = 0, rank = (uint32_t)(32 * VPL - 1) / 2;
     uint32_t* h = hist[warp];
 #pragma unroll
-    for (int shift = 24; shift >= 0; shift -= 8) {
+    for (int pass = 0; pass < 4; ++pass) {
+        const int shift = pass == 0 ? 23 : pass == 1 ? 15 : pass == 2 ? 7 : 0;
+        const uint32_t dm = pass == 3 ? 127u : 255u;
 #pragma unroll
         for (int q = 0; q < 8; ++q) h[lane + 32 * q] = 0;
         __syncwarp();
 #pragma unroll
-        for (int i = 0; i < VPL; ++i) {
-            const bool in = (u[i] & pmask) == prefix;
-            const uint32_t key = in ? ((u[i] >> shift) & 255u) : 256u;
-            const unsigned grp = __match_any_sync(0xffffffffu, key);
-            if (in && lane == __ffs(grp) - 1) atomicAdd(&h[key], (uint32_t)__popc(grp));
-        }
+        for (int i = 0; i < VPL; ++i)
+            if ((u[i] & pmask) == prefix) atomicAdd(&h[(u[i] >> shift) & dm], 1u);
         __syncwarp();
         uint32_t c[8], tot = 0;
 #pragma unroll
@@ -153,83 +150,71 @@ __global__ void __launch_bounds__(256) k_median_warp(const float* __restrict__ P
         sel = __shfl_sync(0xffffffffu, sel, owner);
         nrank = __shfl_sync(0xffffffffu, nrank, owner);
         prefix |= sel << shift;
-        pmask |= 255u << shift;
+        pmask |= dm << shift;
         rank = nrank;
         __syncwarp();
     }
-    if (lane == 0) {
-        const float med = __uint_as_float(prefix);
-        scale[(int64_t)tl * nblk + blk] = (med > 0.f) ? kLn2 / med : 0.f;
-    }
+    const float med = __uint_as_float(prefix);
+    const float sc = (med > 0.f) ? kLn2 / med : 0.f;
+#pragma unroll
+    for (int i = 0; i < VPL; ++i) src[lane + 32 * i] = __uint_as_float(u[i]) * sc;
+    if (lane == 0) scale[(int64_t)tl * nblk + blk] = sc;
 }
 
-// Harmonic sum over a tile of 1024 bins (256 threads x 4 bins, k = k0 + tid + 256 q).
-// For each h = 1..H the whitened bins (k h + H/2) div H of the tile form one
-// contiguous segment; all H segments are staged in shared memory (about 8.5 x
-// the tile) with coalesced loads, then each bin reads its H terms from there.
-constexpr int kHsTile = 1024;
-
+// Incoherent harmonic sum of the whitened spectrum.  With H = nharm_max the h-th
+// term of bin k is Pw[(k h + H/2) div H].  A warp covers 128 consecutive bins as
+// k = k_w + lane + 32 q (q = 0..3), so for each h the four terms sit at
+// ((k_w + lane) h + H/2) div H + 32 q h / H: one index per h plus compile-time
+// offsets, 4H independent coalesced loads per thread.
 template <int NH>
-__global__ void __launch_bounds__(256) k_harmsum_tiled(const float* __restrict__ P,
-                                                       const float* __restrict__ scale, Plan p,
-                                                       int64_t tidx0, Thr thr,
-                                                       Cand* __restrict__ cands, int64_t cap,
-                                                       unsigned long long* __restrict__ count,
-                                                       float* __restrict__ s_out)
+__global__ void __launch_bounds__(256) k_harmsum_direct(const float* __restrict__ Pw, Plan p,
+                                                        int64_t tidx0, Thr thr,
+                                                        Cand* __restrict__ cands, int64_t cap,
+                                                        unsigned long long* __restrict__ count,
+                                                        float* __restrict__ s_out)
 {
     constexpr int LOGNH = (NH == 1) ? 0 : (NH == 2) ? 1 : (NH == 4) ? 2 : (NH == 8) ? 3 : 4;
     constexpr int NLEV = LOGNH + 1;
-    constexpr int SEG = kHsTile * (NH + 1) / 2 + 2 * NH;
-    __shared__ float seg[SEG];
+    constexpr int QN = 4;
     const int tl = blockIdx.y;
-    const int64_t k0 = (int64_t)blockIdx.x * kHsTile;
-    const float* Pt = P + (int64_t)tl * p.M;
-    const float* sc = scale + (int64_t)tl * (p.M >> p.logW);
-    int base[NH];
+    const unsigned lane = threadIdx.x & 31u;
+    const int kb = (blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5)) * (32 * QN) + (int)lane;
+    const float* Pt = Pw + (int64_t)tl * p.M;
+    float S[QN][NLEV];
     {
-        int off = 0;
+        float F[QN][NH];
 #pragma unroll
         for (int h = 1; h <= NH; ++h) {
-            const int64_t s0 = (k0 * h + (NH >> 1)) >> LOGNH;
-            const int64_t s1 = ((k0 + kHsTile - 1) * h + (NH >> 1)) >> LOGNH;
-            const int len = (int)(s1 - s0 + 1);
-            for (int i = threadIdx.x; i < len; i += blockDim.x) {
-                const int64_t b = s0 + i;
-                seg[off + i] = __ldg(Pt + b) * __ldg(sc + (b >> p.logW));
+            const float* ph = Pt + (((int64_t)kb * h + (NH >> 1)) >> LOGNH);
+#pragma unroll
+            for (int q = 0; q < QN; ++q) F[q][h - 1] = __ldg(ph + ((32 * q * h) >> LOGNH));
+        }
+#pragma unroll
+        for (int q = 0; q < QN; ++q) {
+            float s = F[q][NH - 1];
+            S[q][0] = s;
+#pragma unroll
+            for (int L = 1; L < NLEV; ++L) {
+                const int n = 1 << L;
+                const int step = NH / n;
+#pragma unroll
+                for (int h = 1; h <= n; h += 2) s += F[q][h * step - 1];
+                S[q][L] = s;
             }
-            const int64_t kb = k0 + threadIdx.x;
-            base[h - 1] = off + (int)(((kb * h + (NH >> 1)) >> LOGNH) - s0);
-            off += len;
         }
     }
-    __syncthreads();
-    const unsigned lane = threadIdx.x & 31u;
 #pragma unroll
-    for (int q = 0; q < kHsTile / 256; ++q) {
-        const int64_t k = k0 + threadIdx.x + 256 * q;
-        const bool valid = (k >= 1) && (k < p.M);
-        float F[NH];
-#pragma unroll
-        for (int h = 1; h <= NH; ++h) F[h - 1] = seg[base[h - 1] + ((256 * q * h) >> LOGNH)];
-        float S[NLEV];
-        float s = F[NH - 1];
-        S[0] = s;
-#pragma unroll
-        for (int L = 1; L < NLEV; ++L) {
-            const int n = 1 << L;
-            const int step = NH / n;
-#pragma unroll
-            for (int h = 1; h <= n; h += 2) s += F[h * step - 1];
-            S[L] = s;
-        }
-        if (s_out && k < p.M) {
+    for (int q = 0; q < QN; ++q) {
+        const int k = kb + 32 * q;
+        const bool valid = k >= 1;
+        if (s_out) {
 #pragma unroll
             for (int L = 0; L < NLEV; ++L)
-                s_out[((int64_t)tl * NLEV + L) * p.M + k] = valid ? S[L] : 0.f;
+                s_out[((int64_t)tl * NLEV + L) * p.M + k] = valid ? S[q][L] : 0.f;
         }
 #pragma unroll
         for (int L = 0; L < NLEV; ++L) {
-            const bool hit = valid && (S[L] >= thr.v[L]);
+            const bool hit = valid && (S[q][L] >= thr.v[L]);
             const unsigned m = __ballot_sync(0xffffffffu, hit);
             if (m) {
                 const int leader = __ffs(m) - 1;
@@ -244,7 +229,7 @@ __global__ void __launch_bounds__(256) k_harmsum_tiled(const float* __restrict__
                         c.nharm = (uint16_t)(1 << L);
                         c.flags = 0;
                         c.bin = (uint32_t)k;
-                        c.power = S[L];
+                        c.power = S[q][L];
                         cands[pos] = c;
                     }
                 }
@@ -255,7 +240,7 @@ __global__ void __launch_bounds__(256) k_harmsum_tiled(const float* __restrict__
 
 }  // namespace
 
-cudaError_t launch_block_median(const float* P, int nt, const Plan& p, float* scale,
+cudaError_t launch_block_median(float* P, int nt, const Plan& p, float* scale,
                                 cudaStream_t s)
 {
     const int64_t nblk = p.M >> p.logW;
@@ -279,7 +264,8 @@ cudaError_t launch_whitened(const float* P, const float* scale, int nt, const Pl
                             float* out, cudaStream_t s)
 {
     dim3 grid((unsigned)((p.M + 255) / 256), (unsigned)nt);
-    k_whitened<<<grid, 256, 0, s>>>(P, scale, p, out);
+    (void)scale;
+    k_whitened<<<grid, 256, 0, s>>>(P, p, out);
     return cudaGetLastError();
 }
 
@@ -287,13 +273,14 @@ cudaError_t launch_harmsum(const float* P, const float* scale, int nt, int64_t t
                            const Plan& p, const Thr& thr, Cand* cands, int64_t cap,
                            unsigned long long* count, float* s_out, cudaStream_t s)
 {
-    dim3 grid((unsigned)(p.M / kHsTile), (unsigned)nt);
+    (void)scale;
+    dim3 grid((unsigned)(p.M / 1024), (unsigned)nt);  // 8 warps x 128 bins per CTA
     switch (p.nharm) {
-        case 1: k_harmsum_tiled<1><<<grid, 256, 0, s>>>(P, scale, p, tidx0, thr, cands, cap, count, s_out); break;
-        case 2: k_harmsum_tiled<2><<<grid, 256, 0, s>>>(P, scale, p, tidx0, thr, cands, cap, count, s_out); break;
-        case 4: k_harmsum_tiled<4><<<grid, 256, 0, s>>>(P, scale, p, tidx0, thr, cands, cap, count, s_out); break;
-        case 8: k_harmsum_tiled<8><<<grid, 256, 0, s>>>(P, scale, p, tidx0, thr, cands, cap, count, s_out); break;
-        case 16: k_harmsum_tiled<16><<<grid, 256, 0, s>>>(P, scale, p, tidx0, thr, cands, cap, count, s_out); break;
+        case 1: k_harmsum_direct<1><<<grid, 256, 0, s>>>(P, p, tidx0, thr, cands, cap, count, s_out); break;
+        case 2: k_harmsum_direct<2><<<grid, 256, 0, s>>>(P, p, tidx0, thr, cands, cap, count, s_out); break;
+        case 4: k_harmsum_direct<4><<<grid, 256, 0, s>>>(P, p, tidx0, thr, cands, cap, count, s_out); break;
+        case 8: k_harmsum_direct<8><<<grid, 256, 0, s>>>(P, p, tidx0, thr, cands, cap, count, s_out); break;
+        case 16: k_harmsum_direct<16><<<grid, 256, 0, s>>>(P, p, tidx0, thr, cands, cap, count, s_out); break;
         default: return cudaErrorInvalidValue;
     }
     return cudaGetLastError();

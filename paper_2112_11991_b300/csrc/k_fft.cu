@@ -12,8 +12,9 @@
 // consecutive bins is written as one run.
 //
 // Both passes hold a tile of at most 2^14 complex values in shared memory (padded
-// by one element per 16 against bank conflicts) and run radix-4 (+ radix-2)
-// Stockham stages; each thread keeps its EPT = 32 elements in registers across
+// by one element per 16, which makes the strided radix-16 writes conflict-free)
+// and run radix-16 Stockham stages with register butterflies, closed by one
+// radix-8/4/2 stage; each thread keeps its EPT = 32 elements in registers across
 // the barrier between the read and the write of a stage.
 #include <cmath>
 
@@ -34,33 +35,91 @@ __device__ __forceinline__ float2 cmul(float2 a, float2 b)
     return make_float2(a.x * b.x - a.y * b.y, a.x * b.y + a.y * b.x);
 }
 
-template <int RADIX>
-__device__ __forceinline__ void dft(float2* v);
+__device__ __forceinline__ float2 cadd(float2 a, float2 b) { return make_float2(a.x + b.x, a.y + b.y); }
+__device__ __forceinline__ float2 csub(float2 a, float2 b) { return make_float2(a.x - b.x, a.y - b.y); }
+__device__ __forceinline__ float2 mul_negi(float2 a) { return make_float2(a.y, -a.x); }  // a * (-i)
 
-template <>
-__device__ __forceinline__ void dft<2>(float2* v)
+// In-place forward 4-point DFT, natural order in and out.
+__device__ __forceinline__ void dft4(float2& a, float2& b, float2& c, float2& d)
 {
-    const float2 a = v[0], b = v[1];
-    v[0] = make_float2(a.x + b.x, a.y + b.y);
-    v[1] = make_float2(a.x - b.x, a.y - b.y);
+    const float2 s0 = cadd(a, c), s1 = csub(a, c), s2 = cadd(b, d), s3 = csub(b, d);
+    a = cadd(s0, s2);
+    c = csub(s0, s2);
+    b = make_float2(s1.x + s3.y, s1.y - s3.x);  // s1 - i s3
+    d = make_float2(s1.x - s3.y, s1.y + s3.x);  // s1 + i s3
 }
 
-template <>
-__device__ __forceinline__ void dft<4>(float2* v)
-{
-    const float2 a0 = make_float2(v[0].x + v[2].x, v[0].y + v[2].y);
-    const float2 a1 = make_float2(v[0].x - v[2].x, v[0].y - v[2].y);
-    const float2 a2 = make_float2(v[1].x + v[3].x, v[1].y + v[3].y);
-    const float2 a3 = make_float2(v[1].x - v[3].x, v[1].y - v[3].y);
-    v[0] = make_float2(a0.x + a2.x, a0.y + a2.y);
-    v[2] = make_float2(a0.x - a2.x, a0.y - a2.y);
-    v[1] = make_float2(a1.x + a3.y, a1.y - a3.x);  // a1 - i a3
-    v[3] = make_float2(a1.x - a3.y, a1.y + a3.x);  // a1 + i a3
-}
+constexpr float kR2 = 0.70710678118654752440f;  // 1/sqrt(2)
+constexpr float kC8 = 0.92387953251128675613f;  // cos(pi/8)
+constexpr float kS8 = 0.38268343236508977173f;  // sin(pi/8)
 
-// One Stockham stage over 2^lognl lines of length L = 2^logL in shared memory;
-// element (line, pos) lives at buf[pad(line*ls + pos*es)].  Ns = 2^logNs is the
-// length of the sub-transforms already done.  blockDim.x * EPT == lines * L.
+// Radix-R butterflies in registers.  After dft<R>(v), output X[s] sits in
+// v[out_pos<R>(s)] (a fixed register permutation resolved at compile time).
+template <int LOGR>
+struct Radix;
+
+template <>
+struct Radix<1> {
+    static __device__ __forceinline__ void dft(float2* v)
+    {
+        const float2 a = v[0], b = v[1];
+        v[0] = cadd(a, b);
+        v[1] = csub(a, b);
+    }
+    static constexpr __device__ __forceinline__ int out_pos(int s) { return s; }
+};
+
+template <>
+struct Radix<2> {
+    static __device__ __forceinline__ void dft(float2* v) { dft4(v[0], v[1], v[2], v[3]); }
+    static constexpr __device__ __forceinline__ int out_pos(int s) { return s; }
+};
+
+// 8 = 4 x 2: n = 2 n1 + n2, k = k1 + 4 k2
+template <>
+struct Radix<3> {
+    static __device__ __forceinline__ void dft(float2* v)
+    {
+        dft4(v[0], v[2], v[4], v[6]);
+        dft4(v[1], v[3], v[5], v[7]);
+        v[3] = make_float2(kR2 * (v[3].x + v[3].y), kR2 * (v[3].y - v[3].x));    // * W8^1
+        v[5] = mul_negi(v[5]);                                                    // * W8^2
+        v[7] = make_float2(kR2 * (v[7].y - v[7].x), -kR2 * (v[7].x + v[7].y));   // * W8^3
+#pragma unroll
+        for (int k1 = 0; k1 < 4; ++k1) {
+            const float2 a = v[2 * k1], b = v[2 * k1 + 1];
+            v[2 * k1] = cadd(a, b);
+            v[2 * k1 + 1] = csub(a, b);
+        }
+    }
+    static constexpr __device__ __forceinline__ int out_pos(int s) { return 2 * (s & 3) + (s >> 2); }
+};
+
+// 16 = 4 x 4: n = 4 n1 + n2, k = k1 + 4 k2, inner twiddles W16^{n2 k1}
+template <>
+struct Radix<4> {
+    static __device__ __forceinline__ void dft(float2* v)
+    {
+#pragma unroll
+        for (int n2 = 0; n2 < 4; ++n2) dft4(v[n2], v[n2 + 4], v[n2 + 8], v[n2 + 12]);
+        v[5] = cmul(v[5], make_float2(kC8, -kS8));                                   // W16^1
+        v[9] = make_float2(kR2 * (v[9].x + v[9].y), kR2 * (v[9].y - v[9].x));       // W16^2
+        v[13] = cmul(v[13], make_float2(kS8, -kC8));                                 // W16^3
+        v[6] = make_float2(kR2 * (v[6].x + v[6].y), kR2 * (v[6].y - v[6].x));       // W16^2
+        v[10] = mul_negi(v[10]);                                                     // W16^4
+        v[14] = make_float2(kR2 * (v[14].y - v[14].x), -kR2 * (v[14].x + v[14].y)); // W16^6
+        v[7] = cmul(v[7], make_float2(kS8, -kC8));                                   // W16^3
+        v[11] = make_float2(kR2 * (v[11].y - v[11].x), -kR2 * (v[11].x + v[11].y)); // W16^6
+        v[15] = cmul(v[15], make_float2(-kC8, kS8));                                 // W16^9
+#pragma unroll
+        for (int k1 = 0; k1 < 4; ++k1) dft4(v[4 * k1], v[4 * k1 + 1], v[4 * k1 + 2], v[4 * k1 + 3]);
+    }
+    static constexpr __device__ __forceinline__ int out_pos(int s) { return 4 * (s & 3) + (s >> 2); }
+};
+
+// One Stockham stage of radix 2^LOGRADIX over 2^lognl lines of length L = 2^logL in
+// shared memory; element (line, pos) lives at buf[pad(line*ls + pos*es)].  Ns = 2^logNs
+// is the length of the sub-transforms already done.  blockDim.x * EPT == lines * L.
 template <int LOGRADIX, int EPT, bool LINE_FAST>
 __device__ __forceinline__ void fft_stage(float2* buf, int logL, int logNs, int lognl,
                                           int ls, int es, const float2* __restrict__ tw)
@@ -70,7 +129,7 @@ __device__ __forceinline__ void fft_stage(float2* buf, int logL, int logNs, int 
     const int logQ = logL - LOGRADIX;
     const int Q = 1 << logQ;
     const int Ns = 1 << logNs;
-    const int twshift = 12 - logNs - LOGRADIX;  // 4096 / (Ns * RADIX)
+    const int twshift = 13 - logNs - LOGRADIX;  // 8192 / (Ns * RADIX)
     float2 v[EPT];
     int dst[BPT];
 #pragma unroll
@@ -85,41 +144,48 @@ __device__ __forceinline__ void fft_stage(float2* buf, int logL, int logNs, int 
             line = b >> logQ;
         }
         const int k = j & (Ns - 1);
-        const int base = line * ls;
+        const int base = line * ls + j * es;
+        const int qs = Q * es;
 #pragma unroll
         for (int s = 0; s < RADIX; ++s) {
-            float2 x = buf[pad(base + (j + s * Q) * es)];
-            if (s > 0) x = cmul(x, __ldg(tw + ((k * s) << twshift)));
+            float2 x = buf[pad(base + s * qs)];
+            if (s > 0 && logNs > 0) x = cmul(x, __ldg(tw + ((k * s) << twshift)));
             v[i * RADIX + s] = x;
         }
-        dst[i] = base + (((j >> logNs) << (logNs + LOGRADIX)) + k) * es;
+        dst[i] = line * ls + (((j >> logNs) << (logNs + LOGRADIX)) + k) * es;
     }
     __syncthreads();
+    const int nse = Ns * es;
 #pragma unroll
     for (int i = 0; i < BPT; ++i) {
-        dft<RADIX>(v + i * RADIX);
+        Radix<LOGRADIX>::dft(v + i * RADIX);
 #pragma unroll
-        for (int s = 0; s < RADIX; ++s) buf[pad(dst[i] + s * Ns * es)] = v[i * RADIX + s];
+        for (int s = 0; s < RADIX; ++s)
+            buf[pad(dst[i] + s * nse)] = v[i * RADIX + Radix<LOGRADIX>::out_pos(s)];
     }
     __syncthreads();
 }
 
+// Radix-16 stages, then one radix-8/4/2 stage for the remaining factor.
 template <int EPT, bool LINE_FAST>
 __device__ __forceinline__ void smem_fft(float2* buf, int logL, int lognl, int ls, int es,
                                          const float2* __restrict__ tw)
 {
     int logNs = 0;
-    for (; logNs + 2 <= logL; logNs += 2)
-        fft_stage<2, EPT, LINE_FAST>(buf, logL, logNs, lognl, ls, es, tw);
-    if (logNs < logL) fft_stage<1, EPT, LINE_FAST>(buf, logL, logNs, lognl, ls, es, tw);
+    for (; logNs + 4 <= logL; logNs += 4)
+        fft_stage<4, EPT, LINE_FAST>(buf, logL, logNs, lognl, ls, es, tw);
+    const int rem = logL - logNs;
+    if (rem == 3) fft_stage<3, EPT, LINE_FAST>(buf, logL, logNs, lognl, ls, es, tw);
+    else if (rem == 2) fft_stage<2, EPT, LINE_FAST>(buf, logL, logNs, lognl, ls, es, tw);
+    else if (rem == 1) fft_stage<1, EPT, LINE_FAST>(buf, logL, logNs, lognl, ls, es, tw);
 }
 
 __global__ void k_twiddle_init(float2* tw)
 {
     const int t = blockIdx.x * blockDim.x + threadIdx.x;
-    if (t < 4096) {
+    if (t < kTwiddleN) {
         double s, c;
-        sincospi((double)t / 2048.0, &s, &c);  // angle 2 pi t / 4096
+        sincospi((double)t / 4096.0, &s, &c);  // angle 2 pi t / 8192
         tw[t] = make_float2((float)c, (float)-s);
     }
 }
@@ -262,11 +328,11 @@ __global__ void __launch_bounds__(512, 1) k_pass2(const float2* __restrict__ Y, 
     __syncthreads();
     smem_fft<kEPT, false>(sm, logC, logNP + 1, C, 1, tw);
     float* Pt = P + (int64_t)tl * p.M;
-    // W_N^{q + R k2} = W_N^q * W_{2C}^{k2};  W_{2C}^{k2} = tw[k2 * 4096 / (2C)]
+    // W_N^{q + R k2} = W_N^q * W_{2C}^{k2};  W_{2C}^{k2} = tw[k2 * 8192 / (2C)]
     const int ql = threadIdx.x & (NP - 1);
     const int q = q0 + ql;
     const float2 wq = twiddle((uint32_t)q, p.logn);
-    const int twsh = 11 - logC;
+    const int twsh = 12 - logC;
     const int lowl = ql, highl = NP + ql;
     const int items = NP * C;
     for (int it = threadIdx.x; it < items; it += nthr) {
@@ -318,9 +384,9 @@ size_t tile_smem(int logt) { return (size_t)(((1 << logt) + ((1 << logt) >> 4)) 
 
 }  // namespace
 
-cudaError_t launch_twiddle_init(float2* tw4096, cudaStream_t s)
+cudaError_t launch_twiddle_init(float2* tw, cudaStream_t s)
 {
-    k_twiddle_init<<<16, 256, 0, s>>>(tw4096);
+    k_twiddle_init<<<kTwiddleN / 256, 256, 0, s>>>(tw);
     return cudaGetLastError();
 }
 
