@@ -52,6 +52,7 @@ def parse():
     ap.add_argument("--logn", type=int, default=23)
     ap.add_argument("--templates", type=int, default=4096)
     ap.add_argument("--batch", type=int, default=0)
+    ap.add_argument("--log-tile", type=int, default=0)
     ap.add_argument("--no-plain", action="store_true")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--cpu-templates", type=int, default=0)
@@ -260,7 +261,7 @@ def main():
 
     def timed_steps(mode, steps, warmup, profile):
         prm = bps.default_params(mode=mode, batch=args.batch if mode == 0 else 0,
-                                 cand_cap=CAND_CAP)
+                                 cand_cap=CAND_CAP, log_tile=args.log_tile)
         ctx.set_profiling(False)
         for _ in range(warmup):
             rid = ctx.search(sid, bid, prm, stream=stream)
@@ -308,7 +309,7 @@ def main():
     pinned = torch.from_numpy(w.series).pin_memory()
     e2e_ms = []
     d2h = 0
-    prm = bps.default_params(batch=args.batch, cand_cap=CAND_CAP)
+    prm = bps.default_params(batch=args.batch, cand_cap=CAND_CAP, log_tile=args.log_tile)
     for i in range(args.warmup + args.steps):
         torch.cuda.synchronize(dev)
         t0 = time.perf_counter()

@@ -122,7 +122,7 @@ struct Radix<4> {
 // is the length of the sub-transforms already done.  blockDim.x * EPT == lines * L.
 template <int LOGRADIX, int EPT, bool LINE_FAST>
 __device__ __forceinline__ void fft_stage(float2* buf, int logL, int logNs, int lognl,
-                                          int ls, int es, const float2* __restrict__ tw)
+                                          int ls, int es, int skew, const float2* __restrict__ tw)
 {
     constexpr int RADIX = 1 << LOGRADIX;
     constexpr int BPT = EPT / RADIX;
@@ -131,7 +131,7 @@ __device__ __forceinline__ void fft_stage(float2* buf, int logL, int logNs, int 
     const int Ns = 1 << logNs;
     const int twshift = 13 - logNs - LOGRADIX;  // 8192 / (Ns * RADIX)
     float2 v[EPT];
-    int dst[BPT];
+    int dst[BPT], lskv[BPT];
 #pragma unroll
     for (int i = 0; i < BPT; ++i) {
         const int b = threadIdx.x + i * blockDim.x;
@@ -146,13 +146,15 @@ __device__ __forceinline__ void fft_stage(float2* buf, int logL, int logNs, int 
         const int k = j & (Ns - 1);
         const int base = line * ls + j * es;
         const int qs = Q * es;
+        const int lsk = line * skew;
 #pragma unroll
         for (int s = 0; s < RADIX; ++s) {
-            float2 x = buf[pad(base + s * qs)];
+            float2 x = buf[pad(base + s * qs) + lsk];
             if (s > 0 && logNs > 0) x = cmul(x, __ldg(tw + ((k * s) << twshift)));
             v[i * RADIX + s] = x;
         }
         dst[i] = line * ls + (((j >> logNs) << (logNs + LOGRADIX)) + k) * es;
+        lskv[i] = lsk;
     }
     __syncthreads();
     const int nse = Ns * es;
@@ -161,7 +163,7 @@ __device__ __forceinline__ void fft_stage(float2* buf, int logL, int logNs, int 
         Radix<LOGRADIX>::dft(v + i * RADIX);
 #pragma unroll
         for (int s = 0; s < RADIX; ++s)
-            buf[pad(dst[i] + s * nse)] = v[i * RADIX + Radix<LOGRADIX>::out_pos(s)];
+            buf[pad(dst[i] + s * nse) + lskv[i]] = v[i * RADIX + Radix<LOGRADIX>::out_pos(s)];
     }
     __syncthreads();
 }
@@ -169,15 +171,15 @@ __device__ __forceinline__ void fft_stage(float2* buf, int logL, int logNs, int 
 // Radix-16 stages, then one radix-8/4/2 stage for the remaining factor.
 template <int EPT, bool LINE_FAST>
 __device__ __forceinline__ void smem_fft(float2* buf, int logL, int lognl, int ls, int es,
-                                         const float2* __restrict__ tw)
+                                         int skew, const float2* __restrict__ tw)
 {
     int logNs = 0;
     for (; logNs + 4 <= logL; logNs += 4)
-        fft_stage<4, EPT, LINE_FAST>(buf, logL, logNs, lognl, ls, es, tw);
+        fft_stage<4, EPT, LINE_FAST>(buf, logL, logNs, lognl, ls, es, skew, tw);
     const int rem = logL - logNs;
-    if (rem == 3) fft_stage<3, EPT, LINE_FAST>(buf, logL, logNs, lognl, ls, es, tw);
-    else if (rem == 2) fft_stage<2, EPT, LINE_FAST>(buf, logL, logNs, lognl, ls, es, tw);
-    else if (rem == 1) fft_stage<1, EPT, LINE_FAST>(buf, logL, logNs, lognl, ls, es, tw);
+    if (rem == 3) fft_stage<3, EPT, LINE_FAST>(buf, logL, logNs, lognl, ls, es, skew, tw);
+    else if (rem == 2) fft_stage<2, EPT, LINE_FAST>(buf, logL, logNs, lognl, ls, es, skew, tw);
+    else if (rem == 1) fft_stage<1, EPT, LINE_FAST>(buf, logL, logNs, lognl, ls, es, skew, tw);
 }
 
 __global__ void k_twiddle_init(float2* tw)
@@ -267,7 +269,7 @@ __global__ void __launch_bounds__(512, 1) k_pass1(SeriesView x, const Anchor* __
         }
     }
     __syncthreads();
-    smem_fft<kEPT, true>(sm, p.logR, logG, 1, G, tw);
+    smem_fft<kEPT, true>(sm, p.logR, logG, 1, G, 0, tw);
     // four-step twiddle W_M^{j2 k1}: j2 is fixed per thread, k1 steps by nthr/G
     const int g = threadIdx.x & (G - 1);
     const uint32_t j2 = (uint32_t)(c0 + g);
@@ -316,17 +318,23 @@ __global__ void __launch_bounds__(512, 1) k_pass2(const float2* __restrict__ Y, 
     const int q0 = blockIdx.x << logNP;
     const int nthr = blockDim.x;
     const float2* Yt = Y + (int64_t)tl * p.M;
-    // lines [0, NP): low rows q0 + l ; lines [NP, 2NP): their mirrors
+    // lines [0, NP): low rows q0 + l ; lines [NP, 2NP): their mirrors.  Line l starts
+    // at pad(l*C) + l*skew: the skew spreads the NP lines a warp reads in the split
+    // phase over distinct banks.
+    const int skew = 32 >> logNP;
 #pragma unroll 8
-    for (int i = 0; i < kEPT; ++i) {
-        const int e = threadIdx.x + i * nthr;
+    for (int i = 0; i < kEPT / 2; ++i) {
+        const int e = 2 * (threadIdx.x + i * nthr);
         const int line = e >> logC, j2 = e & (C - 1);
         const int q = q0 + (line & (NP - 1));
         const int row = (line < NP) ? q : (q == 0 ? (R >> 1) : R - q);
-        sm[pad(e)] = __ldg(Yt + ((int64_t)row << logC) + j2);
+        const float4 z2 = __ldg(reinterpret_cast<const float4*>(Yt + ((int64_t)row << logC) + j2));
+        const int a = pad(e) + line * skew;
+        sm[a] = make_float2(z2.x, z2.y);
+        sm[a + 1] = make_float2(z2.z, z2.w);
     }
     __syncthreads();
-    smem_fft<kEPT, false>(sm, logC, logNP + 1, C, 1, tw);
+    smem_fft<kEPT, false>(sm, logC, logNP + 1, C, 1, skew, tw);
     float* Pt = P + (int64_t)tl * p.M;
     // W_N^{q + R k2} = W_N^q * W_{2C}^{k2};  W_{2C}^{k2} = tw[k2 * 8192 / (2C)]
     const int ql = threadIdx.x & (NP - 1);
@@ -334,6 +342,7 @@ __global__ void __launch_bounds__(512, 1) k_pass2(const float2* __restrict__ Y, 
     const float2 wq = twiddle((uint32_t)q, p.logn);
     const int twsh = 12 - logC;
     const int lowl = ql, highl = NP + ql;
+    const int lo0 = lowl * skew, hi0 = highl * skew;
     const int items = NP * C;
     for (int it = threadIdx.x; it < items; it += nthr) {
         const int k2 = it >> logNP;
@@ -341,15 +350,16 @@ __global__ void __launch_bounds__(512, 1) k_pass2(const float2* __restrict__ Y, 
             const int64_t k = q + ((int64_t)k2 << logR);
             const float2 w = cmul(wq, __ldg(tw + (k2 << twsh)));
             float pa, pb;
-            power_pair(sm[pad(lowl * C + k2)], sm[pad(highl * C + (C - 1 - k2))], w, pa, pb);
+            power_pair(sm[pad(lowl * C + k2) + lo0], sm[pad(highl * C + (C - 1 - k2)) + hi0], w,
+                       pa, pb);
             Pt[k] = pa;
             Pt[p.M - k] = pb;
         } else {
             if (k2 <= (C >> 1)) {  // row 0: bins R k2 and M - R k2
                 const int64_t k = (int64_t)k2 << logR;
                 float pa, pb;
-                power_pair(sm[pad(k2)], sm[pad((C - k2) & (C - 1))], __ldg(tw + (k2 << twsh)),
-                           pa, pb);
+                power_pair(sm[pad(k2) + lo0], sm[pad((C - k2) & (C - 1)) + lo0],
+                           __ldg(tw + (k2 << twsh)), pa, pb);
                 if (k2 == 0) {
                     Pt[0] = 0.f;
                 } else {
@@ -362,7 +372,8 @@ __global__ void __launch_bounds__(512, 1) k_pass2(const float2* __restrict__ Y, 
                 const float2 w =
                     cmul(twiddle((uint32_t)(R >> 1), p.logn), __ldg(tw + (k2 << twsh)));
                 float pa, pb;
-                power_pair(sm[pad(highl * C + k2)], sm[pad(highl * C + (C - 1 - k2))], w, pa, pb);
+                power_pair(sm[pad(highl * C + k2) + hi0], sm[pad(highl * C + (C - 1 - k2)) + hi0],
+                           w, pa, pb);
                 Pt[k] = pa;
                 Pt[p.M - k] = pb;
             }
@@ -380,7 +391,8 @@ __global__ void k_power_r2c(const float2* __restrict__ X, Plan p, float* __restr
     P[(int64_t)tl * p.M + k] = (k == 0) ? 0.f : z.x * z.x + z.y * z.y;
 }
 
-size_t tile_smem(int logt) { return (size_t)(((1 << logt) + ((1 << logt) >> 4)) * sizeof(float2)); }
+// padded tile plus the pass-2 line skew (at most 32 complex in total)
+size_t tile_smem(int logt) { return (size_t)(((1 << logt) + ((1 << logt) >> 4) + 64) * sizeof(float2)); }
 
 }  // namespace
 
