@@ -91,9 +91,9 @@ __device__ __forceinline__ Anchor load_anchor(const Anchor* __restrict__ anc, in
 }
 
 // Gathered sample x[idx] (the series mean outside [0, n)), FP32 or FP16+scale.
-__device__ __forceinline__ float gather_sample(const SeriesView& x, int64_t n, int64_t idx)
+__device__ __forceinline__ float gather_sample(const SeriesView& x, int n, int idx)
 {
-    if (idx < 0 || idx >= n) return x.fill;
+    if ((unsigned)idx >= (unsigned)n) return x.fill;
     if (x.f32) return __ldg(x.f32 + idx);
     const __half h = __ushort_as_half(__ldg(x.f16 + idx));
     return __half2float(h) * __ldg(x.scale + (idx >> 12));

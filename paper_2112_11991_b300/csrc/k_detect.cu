@@ -185,7 +185,7 @@ __global__ void __launch_bounds__(256) k_harmsum_direct(const float* __restrict_
         float F[QN][NH];
 #pragma unroll
         for (int h = 1; h <= NH; ++h) {
-            const float* ph = Pt + (((int64_t)kb * h + (NH >> 1)) >> LOGNH);
+            const float* ph = Pt + ((kb * h + (NH >> 1)) >> LOGNH);  // kb*h < 2^28
 #pragma unroll
             for (int q = 0; q < QN; ++q) F[q][h - 1] = __ldg(ph + ((32 * q * h) >> LOGNH));
         }
@@ -203,15 +203,26 @@ __global__ void __launch_bounds__(256) k_harmsum_direct(const float* __restrict_
             }
         }
     }
+    if (s_out) {
+#pragma unroll
+        for (int q = 0; q < QN; ++q) {
+            const int k = kb + 32 * q;
+#pragma unroll
+            for (int L = 0; L < NLEV; ++L)
+                s_out[((int64_t)tl * NLEV + L) * p.M + k] = (k >= 1) ? S[q][L] : 0.f;
+        }
+    }
+    // threshold: one warp vote for all levels and bins first (detections are rare)
+    bool any = false;
+#pragma unroll
+    for (int q = 0; q < QN; ++q)
+#pragma unroll
+        for (int L = 0; L < NLEV; ++L) any |= (S[q][L] >= thr.v[L]) && (kb + 32 * q >= 1);
+    if (!__any_sync(0xffffffffu, any)) return;
 #pragma unroll
     for (int q = 0; q < QN; ++q) {
         const int k = kb + 32 * q;
         const bool valid = k >= 1;
-        if (s_out) {
-#pragma unroll
-            for (int L = 0; L < NLEV; ++L)
-                s_out[((int64_t)tl * NLEV + L) * p.M + k] = valid ? S[q][L] : 0.f;
-        }
 #pragma unroll
         for (int L = 0; L < NLEV; ++L) {
             const bool hit = valid && (S[q][L] >= thr.v[L]);

@@ -118,8 +118,9 @@ struct Radix<4> {
 };
 
 // One Stockham stage of radix 2^LOGRADIX over 2^lognl lines of length L = 2^logL in
-// shared memory; element (line, pos) lives at buf[pad(line*ls + pos*es)].  Ns = 2^logNs
-// is the length of the sub-transforms already done.  blockDim.x * EPT == lines * L.
+// shared memory; element (line, pos) lives at buf[pad(line*ls + pos*es) + line*skew].
+// Ns = 2^logNs is the length of the sub-transforms already done.
+// blockDim.x * EPT == lines * L.
 template <int LOGRADIX, int EPT, bool LINE_FAST>
 __device__ __forceinline__ void fft_stage(float2* buf, int logL, int logNs, int lognl,
                                           int ls, int es, int skew, const float2* __restrict__ tw)
@@ -148,10 +149,19 @@ __device__ __forceinline__ void fft_stage(float2* buf, int logL, int logNs, int 
         const int qs = Q * es;
         const int lsk = line * skew;
 #pragma unroll
-        for (int s = 0; s < RADIX; ++s) {
-            float2 x = buf[pad(base + s * qs) + lsk];
-            if (s > 0 && logNs > 0) x = cmul(x, __ldg(tw + ((k * s) << twshift)));
-            v[i * RADIX + s] = x;
+        for (int s = 0; s < RADIX; ++s) v[i * RADIX + s] = buf[pad(base + s * qs) + lsk];
+        if (logNs > 0) {
+            // twiddles W^{k s}, s = 1..RADIX-1, from one table load: W^{2^m} by squaring,
+            // the others as products of two lower powers (at most 4 products deep)
+            float2 w[RADIX];
+            w[1] = __ldg(tw + (k << twshift));
+#pragma unroll
+            for (int s = 2; s < RADIX; ++s) {
+                const int hb = (s & (s - 1)) == 0 ? (s >> 1) : (1 << (31 - __clz(s)));
+                w[s] = cmul(w[hb], w[s - hb]);
+            }
+#pragma unroll
+            for (int s = 1; s < RADIX; ++s) v[i * RADIX + s] = cmul(v[i * RADIX + s], w[s]);
         }
         dst[i] = line * ls + (((j >> logNs) << (logNs + LOGRADIX)) + k) * es;
         lskv[i] = lsk;
@@ -261,7 +271,7 @@ __global__ void __launch_bounds__(512, 1) k_pass1(SeriesView x, const Anchor* __
         }
         float v[2 * CH];
 #pragma unroll
-        for (int q = 0; q < 2 * CH; ++q) v[q] = gather_sample(x, p.n, id[q]);
+        for (int q = 0; q < 2 * CH; ++q) v[q] = gather_sample(x, (int)p.n, id[q]);
 #pragma unroll
         for (int i = 0; i < CH; ++i) {
             const int e = threadIdx.x + (c + i) * nthr;

@@ -128,7 +128,7 @@ __global__ void k_resample(SeriesView x, const Anchor* __restrict__ anc, Plan p,
     const Anchor a = at[b];
     bool precise;
     const int k = off_round(a, (int)(m - anchor_centre(b, p.logB)), precise);
-    out[(int64_t)tl * p.n + m] = gather_sample(x, p.n, m + a.I + k);
+    out[(int64_t)tl * p.n + m] = gather_sample(x, (int)p.n, (int)(m + a.I + k));
 }
 
 __global__ void k_series_sum(const float* __restrict__ x, int64_t n, double* __restrict__ sum)
