@@ -298,10 +298,12 @@ def main():
 
     plain = None
     if not args.no_plain:
-        pms, pstats, pc = timed_steps(1, max(2, min(args.steps, 3)), 1, False)
+        pms, pstats, pc = timed_steps(1, max(2, min(args.steps, 3)), 1, True)
         ptot = allmax(ws, sum(pms) / 1e3)
         plain = {"value": K * ws * len(pms) / ptot, "unit": UNIT,
                  "ms_per_step": statistics.mean(pms), "candidates": pc,
+                 "stage_ms_per_step": {k: sum(s["stage_ms"][k] for s in pstats) / len(pstats)
+                                       for k in bps.STAGES},
                  "form": "index map + gather kernel -> cuFFT R2C -> power -> same median/harmonic-sum kernels, one template per launch"}
 
     # end to end through the public API with host buffers: pinned series H2D, bank, search,
