@@ -53,6 +53,7 @@ def parse():
     ap.add_argument("--templates", type=int, default=4096)
     ap.add_argument("--batch", type=int, default=0)
     ap.add_argument("--log-tile", type=int, default=0)
+    ap.add_argument("--log-tile2", type=int, default=0)
     ap.add_argument("--no-plain", action="store_true")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--cpu-templates", type=int, default=0)
@@ -261,7 +262,8 @@ def main():
 
     def timed_steps(mode, steps, warmup, profile):
         prm = bps.default_params(mode=mode, batch=args.batch if mode == 0 else 0,
-                                 cand_cap=CAND_CAP, log_tile=args.log_tile)
+                                 cand_cap=CAND_CAP, log_tile=args.log_tile,
+                                 log_tile2=args.log_tile2)
         ctx.set_profiling(False)
         for _ in range(warmup):
             rid = ctx.search(sid, bid, prm, stream=stream)
@@ -311,7 +313,8 @@ def main():
     pinned = torch.from_numpy(w.series).pin_memory()
     e2e_ms = []
     d2h = 0
-    prm = bps.default_params(batch=args.batch, cand_cap=CAND_CAP, log_tile=args.log_tile)
+    prm = bps.default_params(batch=args.batch, cand_cap=CAND_CAP, log_tile=args.log_tile,
+                                 log_tile2=args.log_tile2)
     for i in range(args.warmup + args.steps):
         torch.cuda.synchronize(dev)
         t0 = time.perf_counter()

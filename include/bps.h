@@ -90,9 +90,9 @@ typedef struct {
     int64_t cand_cap;      /* device candidate capacity of the request (>= 1)       */
     int32_t precision;     /* reserved, 0 (the storage precision is the series')    */
     int32_t batch;         /* templates per launch batch; 0 = library's choice       */
-    int32_t log_tile;      /* FFT tile of 2^log_tile complex values per CTA: 13 or   */
-                           /* 14; 0 = library's choice (13)                           */
-    int32_t reserved;      /* 0                                                       */
+    int32_t log_tile;      /* FFT pass-1 tile: 2^log_tile complex values per CTA,    */
+                           /* 13 or 14; 0 = library's choice (14)                     */
+    int32_t log_tile2;     /* FFT pass-2 tile, 13 or 14; 0 = library's choice (13)   */
 } bps_search_params;
 
 typedef struct bps_ctx bps_ctx;

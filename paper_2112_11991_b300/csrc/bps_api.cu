@@ -155,8 +155,9 @@ int check_params(bps_ctx* ctx, const bps_search_params* pr, int64_t n)
     if (pr->mode != BPS_MODE_FUSED && pr->mode != BPS_MODE_PLAIN)
         return fail(ctx, BPS_ERR_INVALID_ARG, "unknown mode %d", pr->mode);
     if (pr->batch < 0) return fail(ctx, BPS_ERR_INVALID_ARG, "batch must be >= 0");
-    if (pr->log_tile != 0 && pr->log_tile != 13 && pr->log_tile != 14)
-        return fail(ctx, BPS_ERR_INVALID_ARG, "log_tile must be 0, 13 or 14");
+    if ((pr->log_tile != 0 && pr->log_tile != 13 && pr->log_tile != 14) ||
+        (pr->log_tile2 != 0 && pr->log_tile2 != 13 && pr->log_tile2 != 14))
+        return fail(ctx, BPS_ERR_INVALID_ARG, "log_tile and log_tile2 must be 0, 13 or 14");
     return BPS_OK;
 }
 
@@ -181,7 +182,7 @@ int make_plan(bps_ctx* ctx, const Series& s, const Bank& b, const bps_search_par
     p.logn = ilog2(s.n);
     p.M = s.n / 2;
     p.logM = p.logn - 1;
-    plan_geometry(p, pr.log_tile ? pr.log_tile : 13);
+    plan_geometry(p, pr.log_tile ? pr.log_tile : 14, pr.log_tile2 ? pr.log_tile2 : 13);
     p.logW = ilog2(pr.whiten_block);
     p.nharm = pr.nharm_max;
     p.lognh = ilog2(pr.nharm_max);

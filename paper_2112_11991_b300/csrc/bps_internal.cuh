@@ -43,7 +43,8 @@ struct Plan {
     int logR, logC; // M = R * C (four-step: R-point column FFTs, C-point row FFTs)
     int logG;       // columns per CTA in pass 1
     int logNP;      // row pairs per CTA in pass 2
-    int logTile;    // complex values per CTA tile in both passes (13 or 14)
+    int logTile;    // complex values per CTA tile of pass 1 (13 or 14)
+    int logTile2;   // complex values per CTA tile of pass 2 (13 or 14)
     int logB;       // anchor block length B (samples)
     int64_t nanchor;// N / B
     int logW;       // whitening block W (bins)
@@ -53,13 +54,15 @@ struct Plan {
     double tsamp;
 };
 
-// Four-step split of the packed FFT, M = R * C, with CTA tiles of T = 2^logTile complex
-// values in shared memory (13: 256 threads, two CTAs per SM; 14: 512 threads, one):
-// C = 2^min(10, logM - 5) row length (pass 2), R <= 2^13 column length (pass 1),
-// G = T / R adjacent columns per pass-1 CTA, NP = T / (2C) row pairs per pass-2 CTA.
-inline void plan_geometry(Plan& p, int logTile = 13)
+// Four-step split of the packed FFT, M = R * C, with CTA tiles of 2^logTile (pass 1)
+// and 2^logTile2 (pass 2) complex values in shared memory (13: 256 threads, two CTAs
+// per SM; 14: 512 threads, one): C = 2^min(10, logM - 5) row length (pass 2),
+// R <= 2^13 column length (pass 1), G = tile1 / R adjacent columns per pass-1 CTA,
+// NP = tile2 / (2C) row pairs per pass-2 CTA.
+inline void plan_geometry(Plan& p, int logTile = 14, int logTile2 = 13)
 {
     p.logTile = logTile;
+    p.logTile2 = logTile2;
     p.logC = p.logM - 5 < 10 ? p.logM - 5 : 10;
     p.logR = p.logM - p.logC;
     if (p.logR > 13) {
@@ -68,7 +71,7 @@ inline void plan_geometry(Plan& p, int logTile = 13)
     }
     const int lt = logTile > p.logR ? logTile : p.logR;  // a column must fit one tile
     p.logG = p.logC < lt - p.logR ? p.logC : lt - p.logR;
-    p.logNP = (lt - 1 - p.logC) < (p.logR - 1) ? (lt - 1 - p.logC) : (p.logR - 1);
+    p.logNP = (logTile2 - 1 - p.logC) < (p.logR - 1) ? (logTile2 - 1 - p.logC) : (p.logR - 1);
     if (p.logNP < 0) p.logNP = 0;
 }
 

@@ -97,7 +97,7 @@ template <int VPL>
 __global__ void __launch_bounds__(256) k_median_warp(float* __restrict__ P, Plan p,
                                                      float* __restrict__ scale)
 {
-    __shared__ uint32_t hist[8][256];
+    __shared__ uint32_t hist[8][288];  // bin b at b + b/8: conflict-free scan reads
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
     const int tl = blockIdx.y;
     const int64_t nblk = p.M >> p.logW;
@@ -114,16 +114,20 @@ __global__ void __launch_bounds__(256) k_median_warp(float* __restrict__ P, Plan
         const int shift = pass == 0 ? 23 : pass == 1 ? 15 : pass == 2 ? 7 : 0;
         const uint32_t dm = pass == 3 ? 127u : 255u;
 #pragma unroll
-        for (int q = 0; q < 8; ++q) h[lane + 32 * q] = 0;
+        for (int q = 0; q < 9; ++q) h[lane + 32 * q] = 0;
         __syncwarp();
 #pragma unroll
-        for (int i = 0; i < VPL; ++i)
-            if ((u[i] & pmask) == prefix) atomicAdd(&h[(u[i] >> shift) & dm], 1u);
+        for (int i = 0; i < VPL; ++i) {
+            if ((u[i] & pmask) == prefix) {
+                const uint32_t dg = (u[i] >> shift) & dm;
+                atomicAdd(&h[dg + (dg >> 3)], 1u);
+            }
+        }
         __syncwarp();
         uint32_t c[8], tot = 0;
 #pragma unroll
         for (int q = 0; q < 8; ++q) {
-            c[q] = h[8 * lane + q];
+            c[q] = h[9 * lane + q];
             tot += c[q];
         }
         uint32_t inc = tot;
@@ -162,11 +166,11 @@ __global__ void __launch_bounds__(256) k_median_warp(float* __restrict__ P, Plan
 }
 
 // Incoherent harmonic sum of the whitened spectrum.  With H = nharm_max the h-th
-// term of bin k is Pw[(k h + H/2) div H].  A warp covers 128 consecutive bins as
-// k = k_w + lane + 32 q (q = 0..3), so for each h the four terms sit at
+// term of bin k is Pw[(k h + H/2) div H].  A warp covers 32 QN consecutive bins as
+// k = k_w + lane + 32 q (q < QN), so for each h the QN terms sit at
 // ((k_w + lane) h + H/2) div H + 32 q h / H: one index per h plus compile-time
-// offsets, 4H independent coalesced loads per thread.
-template <int NH>
+// offsets, QN H independent coalesced loads per thread.
+template <int NH, int QN>
 __global__ void __launch_bounds__(256) k_harmsum_direct(const float* __restrict__ Pw, Plan p,
                                                         int64_t tidx0, Thr thr,
                                                         Cand* __restrict__ cands, int64_t cap,
@@ -175,7 +179,6 @@ __global__ void __launch_bounds__(256) k_harmsum_direct(const float* __restrict_
 {
     constexpr int LOGNH = (NH == 1) ? 0 : (NH == 2) ? 1 : (NH == 4) ? 2 : (NH == 8) ? 3 : 4;
     constexpr int NLEV = LOGNH + 1;
-    constexpr int QN = 4;
     const int tl = blockIdx.y;
     const unsigned lane = threadIdx.x & 31u;
     const int kb = (blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5)) * (32 * QN) + (int)lane;
@@ -285,13 +288,14 @@ cudaError_t launch_harmsum(const float* P, const float* scale, int nt, int64_t t
                            unsigned long long* count, float* s_out, cudaStream_t s)
 {
     (void)scale;
-    dim3 grid((unsigned)(p.M / 1024), (unsigned)nt);  // 8 warps x 128 bins per CTA
+    constexpr int QN = 2;  // bins per thread: a CTA of 8 warps covers 256 * QN bins
+    dim3 grid((unsigned)(p.M / (256 * QN)), (unsigned)nt);
     switch (p.nharm) {
-        case 1: k_harmsum_direct<1><<<grid, 256, 0, s>>>(P, p, tidx0, thr, cands, cap, count, s_out); break;
-        case 2: k_harmsum_direct<2><<<grid, 256, 0, s>>>(P, p, tidx0, thr, cands, cap, count, s_out); break;
-        case 4: k_harmsum_direct<4><<<grid, 256, 0, s>>>(P, p, tidx0, thr, cands, cap, count, s_out); break;
-        case 8: k_harmsum_direct<8><<<grid, 256, 0, s>>>(P, p, tidx0, thr, cands, cap, count, s_out); break;
-        case 16: k_harmsum_direct<16><<<grid, 256, 0, s>>>(P, p, tidx0, thr, cands, cap, count, s_out); break;
+        case 1: k_harmsum_direct<1, QN><<<grid, 256, 0, s>>>(P, p, tidx0, thr, cands, cap, count, s_out); break;
+        case 2: k_harmsum_direct<2, QN><<<grid, 256, 0, s>>>(P, p, tidx0, thr, cands, cap, count, s_out); break;
+        case 4: k_harmsum_direct<4, QN><<<grid, 256, 0, s>>>(P, p, tidx0, thr, cands, cap, count, s_out); break;
+        case 8: k_harmsum_direct<8, QN><<<grid, 256, 0, s>>>(P, p, tidx0, thr, cands, cap, count, s_out); break;
+        case 16: k_harmsum_direct<16, QN><<<grid, 256, 0, s>>>(P, p, tidx0, thr, cands, cap, count, s_out); break;
         default: return cudaErrorInvalidValue;
     }
     return cudaGetLastError();
