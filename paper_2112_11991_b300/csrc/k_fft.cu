@@ -210,11 +210,70 @@ __device__ __forceinline__ float2 twiddle(uint32_t t, int logD)
     return make_float2(c, -s);
 }
 
-// Pass 1: index map + gather of 2G consecutive samples per row, R-point column
-// FFTs over j1 for G adjacent columns, four-step twiddle, coalesced store.
-// Each thread first evaluates the index map of a chunk of its samples (anchor
-// loads and arithmetic, independent), fixes the rare near-boundary ones with the
-// compensated evaluation, then issues all the chunk's gathers before storing them.
+// Pass 1: index map + gather fused into the first radix-16 stage, middle radix-16
+// stages in shared memory, last stage fused with the four-step twiddle and the
+// coalesced store of Y.  Column FFT length R = 2^logR over G adjacent columns;
+// stages: 16, 16 x k, 2^r with 4 + 4k + r = logR, r in [1, 4].
+//
+// First stage (Ns = 1): butterfly (g, j), j < R/16, takes rows j + s R/16 of
+// column g, s = 0..15.  Each thread gathers the 32 samples of one butterfly
+// (index map fast path for all of them, compensated branch for the rare
+// near-boundary ones), transforms them in registers and writes the 16 outputs.
+template <int LOGR_LAST>
+__device__ __forceinline__ void pass1_last_stage(const float2* __restrict__ sm, const Plan& p,
+                                                 int c0, int logNs, const float2* __restrict__ tw,
+                                                 float2* __restrict__ Yt)
+{
+    constexpr int RL = 1 << LOGR_LAST;
+    constexpr int BPT = kEPT / RL;
+    const int logG = p.logG;
+    const int G = 1 << logG;
+    const int Ns = 1 << logNs;  // = R / RL: j < Ns, outputs at k1 = j + s Ns
+    const int twshift = 13 - logNs - LOGR_LAST;
+    const uint32_t Mm = (uint32_t)(p.M - 1);
+#pragma unroll
+    for (int i = 0; i < BPT; ++i) {
+        const int b = threadIdx.x + i * blockDim.x;
+        const int g = b & (G - 1);
+        const int j = b >> logG;
+        float2 v[RL];
+#pragma unroll
+        for (int s = 0; s < RL; ++s) v[s] = sm[pad(g + G * (j + s * Ns))];
+        {
+            float2 w[RL];
+            w[1] = __ldg(tw + (j << twshift));
+#pragma unroll
+            for (int s = 2; s < RL; ++s) {
+                const int hb = (s & (s - 1)) == 0 ? (s >> 1) : (1 << (31 - __clz(s)));
+                w[s] = cmul(w[hb], w[s - hb]);
+            }
+#pragma unroll
+            for (int s = 1; s < RL; ++s) v[s] = cmul(v[s], w[s]);
+        }
+        Radix<LOGR_LAST>::dft(v);
+        // four-step twiddle W_M^{j2 k1}, k1 = j + s Ns: W_M^{j2 j} (W_M^{j2 Ns})^s
+        const uint32_t j2 = (uint32_t)(c0 + g);
+        float2 u[RL];
+        u[0] = twiddle((j2 * (uint32_t)j) & Mm, p.logM);
+        if (RL > 1) {
+            float2 st[RL];
+            st[1] = twiddle((j2 * (uint32_t)Ns) & Mm, p.logM);
+#pragma unroll
+            for (int s = 2; s < RL; ++s) {
+                const int hb = (s & (s - 1)) == 0 ? (s >> 1) : (1 << (31 - __clz(s)));
+                st[s] = cmul(st[hb], st[s - hb]);
+            }
+#pragma unroll
+            for (int s = 1; s < RL; ++s) u[s] = cmul(u[0], st[s]);
+        }
+#pragma unroll
+        for (int s = 0; s < RL; ++s) {
+            const int k1 = j + s * Ns;
+            Yt[((int64_t)k1 << p.logC) + j2] = cmul(v[Radix<LOGR_LAST>::out_pos(s)], u[s]);
+        }
+    }
+}
+
 __global__ void __launch_bounds__(512, 1) k_pass1(SeriesView x, const Anchor* __restrict__ anc,
                                                   Plan p, const float2* __restrict__ tw,
                                                   float2* __restrict__ Y)
@@ -223,78 +282,71 @@ __global__ void __launch_bounds__(512, 1) k_pass1(SeriesView x, const Anchor* __
     const int tl = blockIdx.y;
     const int logG = p.logG;
     const int G = 1 << logG;
+    const int logR = p.logR;
+    const int logQ = logR - 4;  // rows between the 16 elements of a first-stage butterfly
     const int nthr = blockDim.x;
     const int c0 = blockIdx.x << logG;
+    const int n = (int)p.n;
+    const int half = 1 << (p.logB - 1);
     const Anchor* at = anc + (int64_t)tl * p.nanchor;
-    constexpr int CH = 8;  // elements per gather chunk (16 samples)
-#pragma unroll
-    for (int c = 0; c < kEPT; c += CH) {
-        int id[2 * CH];
+    constexpr int BPT1 = kEPT / 16;
+#pragma unroll 1
+    for (int i = 0; i < BPT1; ++i) {
+        const int b = threadIdx.x + i * nthr;
+        const int g = b & (G - 1);
+        const int j = b >> logG;
+        int id[32];
         unsigned pm = 0;
 #pragma unroll
-        for (int i = 0; i < CH; ++i) {
-            const int e = threadIdx.x + (c + i) * nthr;
-            const int j1 = e >> logG, g = e & (G - 1);
-            const int m = 2 * ((j1 << p.logC) + c0 + g);
-            const int b = m >> p.logB;
-            const float4 a4 = __ldg(reinterpret_cast<const float4*>(at + b));
-            const float q3 = __ldg(&at[b].q3);
+        for (int s = 0; s < 16; ++s) {
+            const int m = 2 * (((j + (s << logQ)) << p.logC) + c0 + g);
+            const int ab = m >> p.logB;
+            const float4 a4 = __ldg(reinterpret_cast<const float4*>(at + ab));
+            const float q3 = __ldg(&at[ab].q3);
             const int I = __float_as_int(a4.x);
             const float fh = a4.y + 0.5f, L = a4.z, q2 = a4.w;
-            const int d = m - ((b << p.logB) + (1 << (p.logB - 1)));
+            const int d = m - ((ab << p.logB) + half);
 #pragma unroll
             for (int u = 0; u < 2; ++u) {
                 const float df = (float)(d + u);
                 const float xx = fh - df * fmaf(df, fmaf(df, q3, q2), L);
                 const float fl = floorf(xx);
                 const float fr = xx - fl;
-                if (!(fr > kGuard && fr < 1.f - kGuard)) pm |= 1u << (2 * i + u);
-                id[2 * i + u] = m + u + I + (int)fl;
+                if (!(fr > kGuard && fr < 1.f - kGuard)) pm |= 1u << (2 * s + u);
+                id[2 * s + u] = m + u + I + (int)fl;
             }
         }
         if (pm) {
 #pragma unroll
-            for (int i = 0; i < CH; ++i) {
-#pragma unroll
-                for (int u = 0; u < 2; ++u) {
-                    if (pm & (1u << (2 * i + u))) {
-                        const int e = threadIdx.x + (c + i) * nthr;
-                        const int j1 = e >> logG, g = e & (G - 1);
-                        const int m = 2 * ((j1 << p.logC) + c0 + g);
-                        const int b = m >> p.logB;
-                        const Anchor a = at[b];
-                        const int d = m - ((b << p.logB) + (1 << (p.logB - 1)));
-                        id[2 * i + u] = m + u + a.I + off_round_precise(a, d + u);
-                    }
+            for (int q = 0; q < 32; ++q) {
+                if (pm & (1u << q)) {
+                    const int s = q >> 1, u = q & 1;
+                    const int m = 2 * (((j + (s << logQ)) << p.logC) + c0 + g);
+                    const int ab = m >> p.logB;
+                    const Anchor a = at[ab];
+                    const int d = m - ((ab << p.logB) + half);
+                    id[q] = m + u + a.I + off_round_precise(a, d + u);
                 }
             }
         }
-        float v[2 * CH];
+        float2 v[16];
 #pragma unroll
-        for (int q = 0; q < 2 * CH; ++q) v[q] = gather_sample(x, (int)p.n, id[q]);
+        for (int s = 0; s < 16; ++s)
+            v[s] = make_float2(gather_sample(x, n, id[2 * s]), gather_sample(x, n, id[2 * s + 1]));
+        Radix<4>::dft(v);
 #pragma unroll
-        for (int i = 0; i < CH; ++i) {
-            const int e = threadIdx.x + (c + i) * nthr;
-            sm[pad(e)] = make_float2(v[2 * i], v[2 * i + 1]);
-        }
+        for (int s = 0; s < 16; ++s) sm[pad(g + G * (16 * j + s))] = v[Radix<4>::out_pos(s)];
     }
     __syncthreads();
-    smem_fft<kEPT, true>(sm, p.logR, logG, 1, G, 0, tw);
-    // four-step twiddle W_M^{j2 k1}: j2 is fixed per thread, k1 steps by nthr/G
-    const int g = threadIdx.x & (G - 1);
-    const uint32_t j2 = (uint32_t)(c0 + g);
-    const uint32_t k10 = (uint32_t)(threadIdx.x >> logG);
-    const uint32_t dk = (uint32_t)(nthr >> logG);
-    const uint32_t Mm = (uint32_t)(p.M - 1);
-    float2 w = twiddle((j2 * k10) & Mm, p.logM);
-    const float2 st = twiddle((j2 * dk) & Mm, p.logM);
+    int logNs = 4;
+    for (; logNs + 4 < logR; logNs += 4)
+        fft_stage<4, kEPT, true>(sm, logR, logNs, logG, 1, G, 0, tw);
     float2* Yt = Y + (int64_t)tl * p.M;
-#pragma unroll 8
-    for (int i = 0; i < kEPT; ++i) {
-        const int e = threadIdx.x + i * nthr;
-        const int k1 = e >> logG;
-        Yt[((int64_t)k1 << p.logC) + j2] = cmul(sm[pad(e)], w);
-        w = cmul(w, st);
+    switch (logR - logNs) {
+        case 4: pass1_last_stage<4>(sm, p, c0, logNs, tw, Yt); break;
+        case 3: pass1_last_stage<3>(sm, p, c0, logNs, tw, Yt); break;
+        case 2: pass1_last_stage<2>(sm, p, c0, logNs, tw, Yt); break;
+        default: pass1_last_stage<1>(sm, p, c0, logNs, tw, Yt); break;
     }
 }
 
@@ -330,21 +382,38 @@ __global__ void __launch_bounds__(512, 1) k_pass2(const float2* __restrict__ Y, 
     const float2* Yt = Y + (int64_t)tl * p.M;
     // lines [0, NP): low rows q0 + l ; lines [NP, 2NP): their mirrors.  Line l starts
     // at pad(l*C) + l*skew: the skew spreads the NP lines a warp reads in the split
-    // phase over distinct banks.
+    // phase over distinct banks.  The first radix-16 stage (Ns = 1) is fused with the
+    // load: butterfly (line, j) reads elements j + s C/16 of its row straight from Y.
     const int skew = 32 >> logNP;
-#pragma unroll 8
-    for (int i = 0; i < kEPT / 2; ++i) {
-        const int e = 2 * (threadIdx.x + i * nthr);
-        const int line = e >> logC, j2 = e & (C - 1);
+    const int logQ = logC - 4;
+    constexpr int BPT1 = kEPT / 16;
+#pragma unroll 1
+    for (int i = 0; i < BPT1; ++i) {
+        const int b = threadIdx.x + i * nthr;
+        const int j = b & ((1 << logQ) - 1);
+        const int line = b >> logQ;
         const int q = q0 + (line & (NP - 1));
         const int row = (line < NP) ? q : (q == 0 ? (R >> 1) : R - q);
-        const float4 z2 = __ldg(reinterpret_cast<const float4*>(Yt + ((int64_t)row << logC) + j2));
-        const int a = pad(e) + line * skew;
-        sm[a] = make_float2(z2.x, z2.y);
-        sm[a + 1] = make_float2(z2.z, z2.w);
+        const float2* src = Yt + ((int64_t)row << logC) + j;
+        float2 v[16];
+#pragma unroll
+        for (int s = 0; s < 16; ++s) v[s] = __ldg(src + (s << logQ));
+        Radix<4>::dft(v);
+        const int base = line * C + 16 * j;
+        const int lsk = line * skew;
+#pragma unroll
+        for (int s = 0; s < 16; ++s) sm[pad(base + s) + lsk] = v[Radix<4>::out_pos(s)];
     }
     __syncthreads();
-    smem_fft<kEPT, false>(sm, logC, logNP + 1, C, 1, skew, tw);
+    {
+        int logNs = 4;
+        for (; logNs + 4 <= logC; logNs += 4)
+            fft_stage<4, kEPT, false>(sm, logC, logNs, logNP + 1, C, 1, skew, tw);
+        const int rem = logC - logNs;
+        if (rem == 3) fft_stage<3, kEPT, false>(sm, logC, logNs, logNP + 1, C, 1, skew, tw);
+        else if (rem == 2) fft_stage<2, kEPT, false>(sm, logC, logNs, logNP + 1, C, 1, skew, tw);
+        else if (rem == 1) fft_stage<1, kEPT, false>(sm, logC, logNs, logNP + 1, C, 1, skew, tw);
+    }
     float* Pt = P + (int64_t)tl * p.M;
     // W_N^{q + R k2} = W_N^q * W_{2C}^{k2};  W_{2C}^{k2} = tw[k2 * 8192 / (2C)]
     const int ql = threadIdx.x & (NP - 1);
