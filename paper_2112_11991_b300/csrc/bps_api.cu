@@ -48,6 +48,7 @@ struct Request {
     int64_t cap = 0;
     bool synced = false;
     unsigned long long total = 0;
+    unsigned long long status = 0;  // bit 0: a bounded device wait expired
     std::vector<bps_candidate> result;
 };
 
@@ -546,8 +547,8 @@ int bps_search(bps_ctx* ctx, int64_t series_id, int64_t bank_id, const bps_searc
     r.K = b->K;
     r.cap = params->cand_cap;
     CK(cudaMalloc((void**)&r.d_cands, sizeof(Cand) * (size_t)r.cap));
-    CK(cudaMalloc((void**)&r.d_count, sizeof(unsigned long long)));
-    CK(cudaMemsetAsync(r.d_count, 0, sizeof(unsigned long long), st));
+    CK(cudaMalloc((void**)&r.d_count, 2 * sizeof(unsigned long long)));  // count, status
+    CK(cudaMemsetAsync(r.d_count, 0, 2 * sizeof(unsigned long long), st));
     CK(cudaEventCreateWithFlags(&r.done, cudaEventDisableTiming));
     const int nt = params->batch > 0 ? (int)std::min<int64_t>(params->batch, b->K)
                                      : default_batch(p, b->K, params->mode);
@@ -629,7 +630,10 @@ int bps_fetch_candidates(bps_ctx* ctx, int64_t req_id, bps_candidate* out, int64
     CK(cudaSetDevice(ctx->device));
     if (!r.synced) {
         CK(cudaEventSynchronize(r.done));
-        CK(cudaMemcpy(&r.total, r.d_count, sizeof r.total, cudaMemcpyDeviceToHost));
+        unsigned long long cs[2];
+        CK(cudaMemcpy(cs, r.d_count, sizeof cs, cudaMemcpyDeviceToHost));
+        r.total = cs[0];
+        r.status = cs[1];
         const int64_t kept = std::min<int64_t>((int64_t)r.total, r.cap);
         r.result.resize((size_t)kept);
         static_assert(sizeof(Cand) == sizeof(bps_candidate), "candidate layout");
@@ -647,6 +651,9 @@ int bps_fetch_candidates(bps_ctx* ctx, int64_t req_id, bps_candidate* out, int64
     if (out && nw > 0) std::memcpy(out, r.result.data(), sizeof(bps_candidate) * nw);
     if (n_written) *n_written = out ? nw : 0;
     if (n_total) *n_total = (int64_t)r.total;
+    if (r.status & 1ull)
+        return fail(ctx, BPS_ERR_TIMEOUT, "request %lld: a bounded device wait expired; "
+                    "results incomplete", (long long)req_id);
     if ((int64_t)r.total > r.cap)
         return fail(ctx, BPS_ERR_CAND_OVERFLOW, "request %lld found %llu candidates, capacity %lld",
                     (long long)req_id, r.total, (long long)r.cap);
@@ -801,8 +808,8 @@ int bps_harmonic_sums(bps_ctx* ctx, int64_t series_id, int64_t bank_id, int64_t 
     unsigned long long* cnt = nullptr;
     CK(cudaMallocAsync((void**)&so, sizeof(float) * p.M * p.nlev, st));
     CK(cudaMallocAsync((void**)&cd, sizeof(Cand), st));
-    CK(cudaMallocAsync((void**)&cnt, sizeof(unsigned long long), st));
-    CK(cudaMemsetAsync(cnt, 0, sizeof(unsigned long long), st));
+    CK(cudaMallocAsync((void**)&cnt, 2 * sizeof(unsigned long long), st));
+    CK(cudaMemsetAsync(cnt, 0, 2 * sizeof(unsigned long long), st));
     StageTimer tm;
     if ((rc = run_spectrum(ctx, *s, *b, p, params->mode, template_idx, 1, w, st, tm))) return rc;
     Thr th;

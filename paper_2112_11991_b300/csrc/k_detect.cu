@@ -252,6 +252,185 @@ __global__ void __launch_bounds__(256) k_harmsum_direct(const float* __restrict_
     }
 }
 
+// ---- TMA bulk copies into shared memory, completed on an mbarrier (inline PTX) ----
+__device__ __forceinline__ uint32_t smem_u32(const void* p)
+{
+    return (uint32_t)__cvta_generic_to_shared(p);
+}
+
+__device__ __forceinline__ void mbar_init(uint64_t* bar, uint32_t count)
+{
+    asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_u32(bar)), "r"(count)
+                 : "memory");
+    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+}
+
+__device__ __forceinline__ void mbar_expect_tx(uint64_t* bar, uint32_t bytes)
+{
+    asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(smem_u32(bar)),
+                 "r"(bytes)
+                 : "memory");
+}
+
+// 1D bulk copy global -> shared (16-byte aligned addresses, size a multiple of 16)
+__device__ __forceinline__ void tma_load_1d(void* dst, const void* src, uint32_t bytes,
+                                            uint64_t* bar)
+{
+    asm volatile(
+        "cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::"r"(
+            smem_u32(dst)),
+        "l"(src), "r"(bytes), "r"(smem_u32(bar))
+        : "memory");
+}
+
+__device__ __forceinline__ bool mbar_try_wait(uint64_t* bar, uint32_t phase)
+{
+    uint32_t ok;
+    asm volatile(
+        "{\n .reg .pred p;\n mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n"
+        " selp.u32 %0, 1, 0, p;\n}\n"
+        : "=r"(ok)
+        : "r"(smem_u32(bar)), "r"(phase)
+        : "memory");
+    return ok != 0;
+}
+
+// Bounded wait for phase 0 of the barrier: false (and error flag set) after the limit.
+constexpr int kWaitLimit = 1 << 22;
+
+__device__ __forceinline__ bool mbar_wait_bounded(uint64_t* bar, unsigned long long* status)
+{
+    for (int it = 0; it < kWaitLimit; ++it)
+        if (mbar_try_wait(bar, 0)) return true;
+    if (status) atomicOr(status, 1ull);  // BPS_ERR_TIMEOUT reported by the host
+    // the copies may still be in flight: give them a second bounded wait before exiting
+    for (int it = 0; it < kWaitLimit; ++it)
+        if (mbar_try_wait(bar, 0)) break;
+    return false;
+}
+
+// Incoherent harmonic sum of the whitened spectrum over a tile of 1024 bins.  With
+// H = nharm_max the h-th term of bin k is Pw[(k h + H/2) div H]; over the tile these
+// terms form one contiguous segment per h.  One thread issues 16-byte-aligned TMA bulk
+// copies of the H segments into shared memory (about 8.6 x the tile), all threads wait
+// on the mbarrier (bounded; on expiry the status word is flagged and the tile skipped),
+// then each thread sums 4 bins k = k0 + tid + 256 q from shared memory.
+constexpr int kHsTile = 1024;
+
+template <int NH>
+__global__ void __launch_bounds__(256) k_harmsum_tma(const float* __restrict__ Pw, Plan p,
+                                                     int64_t tidx0, Thr thr,
+                                                     Cand* __restrict__ cands, int64_t cap,
+                                                     unsigned long long* __restrict__ count,
+                                                     float* __restrict__ s_out)
+{
+    constexpr int LOGNH = (NH == 1) ? 0 : (NH == 2) ? 1 : (NH == 4) ? 2 : (NH == 8) ? 3 : 4;
+    constexpr int NLEV = LOGNH + 1;
+    constexpr int QN = kHsTile / 256;
+    constexpr int SEG = kHsTile * (NH + 1) / 2 + 8 * NH;
+    __shared__ __align__(128) float seg[SEG];
+    __shared__ __align__(8) uint64_t bar;
+    const int tl = blockIdx.y;
+    const int k0 = blockIdx.x * kHsTile;
+    const float* Pt = Pw + (int64_t)tl * p.M;
+    if (threadIdx.x == 0) mbar_init(&bar, 1);
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        uint32_t total = 0;
+#pragma unroll
+        for (int h = 1; h <= NH; ++h) {
+            const int a = ((k0 * h + (NH >> 1)) >> LOGNH) & ~3;
+            const int b = ((((k0 + kHsTile - 1) * h + (NH >> 1)) >> LOGNH) + 4) & ~3;
+            total += (uint32_t)(b - a) * 4u;
+        }
+        mbar_expect_tx(&bar, total);
+        int off = 0;
+#pragma unroll
+        for (int h = 1; h <= NH; ++h) {
+            const int a = ((k0 * h + (NH >> 1)) >> LOGNH) & ~3;
+            const int b = ((((k0 + kHsTile - 1) * h + (NH >> 1)) >> LOGNH) + 4) & ~3;
+            tma_load_1d(seg + off, Pt + a, (uint32_t)(b - a) * 4u, &bar);
+            off += b - a;
+        }
+    }
+    // per-thread base index of each segment (computed while the copies fly)
+    int base[NH];
+    {
+        int off = 0;
+#pragma unroll
+        for (int h = 1; h <= NH; ++h) {
+            const int a = ((k0 * h + (NH >> 1)) >> LOGNH) & ~3;
+            const int b = ((((k0 + kHsTile - 1) * h + (NH >> 1)) >> LOGNH) + 4) & ~3;
+            base[h - 1] = off + ((((k0 + (int)threadIdx.x) * h + (NH >> 1)) >> LOGNH) - a);
+            off += b - a;
+        }
+    }
+    const bool ok = mbar_wait_bounded(&bar, count + 1);
+    if (!ok) return;
+    const unsigned lane = threadIdx.x & 31u;
+    float S[QN][NLEV];
+#pragma unroll
+    for (int q = 0; q < QN; ++q) {
+        float F[NH];
+#pragma unroll
+        for (int h = 1; h <= NH; ++h) F[h - 1] = seg[base[h - 1] + ((256 * q * h) >> LOGNH)];
+        float s = F[NH - 1];
+        S[q][0] = s;
+#pragma unroll
+        for (int L = 1; L < NLEV; ++L) {
+            const int n = 1 << L;
+            const int step = NH / n;
+#pragma unroll
+            for (int h = 1; h <= n; h += 2) s += F[h * step - 1];
+            S[q][L] = s;
+        }
+    }
+    if (s_out) {
+#pragma unroll
+        for (int q = 0; q < QN; ++q) {
+            const int k = k0 + (int)threadIdx.x + 256 * q;
+#pragma unroll
+            for (int L = 0; L < NLEV; ++L)
+                s_out[((int64_t)tl * NLEV + L) * p.M + k] = (k >= 1) ? S[q][L] : 0.f;
+        }
+    }
+    bool any = false;
+#pragma unroll
+    for (int q = 0; q < QN; ++q)
+#pragma unroll
+        for (int L = 0; L < NLEV; ++L)
+            any |= (S[q][L] >= thr.v[L]) && (k0 + (int)threadIdx.x + 256 * q >= 1);
+    if (!__any_sync(0xffffffffu, any)) return;
+#pragma unroll
+    for (int q = 0; q < QN; ++q) {
+        const int k = k0 + (int)threadIdx.x + 256 * q;
+        const bool valid = k >= 1;
+#pragma unroll
+        for (int L = 0; L < NLEV; ++L) {
+            const bool hit = valid && (S[q][L] >= thr.v[L]);
+            const unsigned m = __ballot_sync(0xffffffffu, hit);
+            if (m) {
+                const int leader = __ffs(m) - 1;
+                unsigned long long b0 = 0;
+                if ((int)lane == leader) b0 = atomicAdd(count, (unsigned long long)__popc(m));
+                b0 = __shfl_sync(0xffffffffu, b0, leader);
+                if (hit) {
+                    const unsigned long long pos = b0 + __popc(m & ((1u << lane) - 1u));
+                    if ((int64_t)pos < cap) {
+                        Cand c;
+                        c.tidx = (uint32_t)(tidx0 + tl);
+                        c.nharm = (uint16_t)(1 << L);
+                        c.flags = 0;
+                        c.bin = (uint32_t)k;
+                        c.power = S[q][L];
+                        cands[pos] = c;
+                    }
+                }
+            }
+        }
+    }
+}
+
 }  // namespace
 
 cudaError_t launch_block_median(float* P, int nt, const Plan& p, float* scale,
@@ -288,14 +467,13 @@ cudaError_t launch_harmsum(const float* P, const float* scale, int nt, int64_t t
                            unsigned long long* count, float* s_out, cudaStream_t s)
 {
     (void)scale;
-    constexpr int QN = 2;  // bins per thread: a CTA of 8 warps covers 256 * QN bins
-    dim3 grid((unsigned)(p.M / (256 * QN)), (unsigned)nt);
+    dim3 grid((unsigned)(p.M / kHsTile), (unsigned)nt);
     switch (p.nharm) {
-        case 1: k_harmsum_direct<1, QN><<<grid, 256, 0, s>>>(P, p, tidx0, thr, cands, cap, count, s_out); break;
-        case 2: k_harmsum_direct<2, QN><<<grid, 256, 0, s>>>(P, p, tidx0, thr, cands, cap, count, s_out); break;
-        case 4: k_harmsum_direct<4, QN><<<grid, 256, 0, s>>>(P, p, tidx0, thr, cands, cap, count, s_out); break;
-        case 8: k_harmsum_direct<8, QN><<<grid, 256, 0, s>>>(P, p, tidx0, thr, cands, cap, count, s_out); break;
-        case 16: k_harmsum_direct<16, QN><<<grid, 256, 0, s>>>(P, p, tidx0, thr, cands, cap, count, s_out); break;
+        case 1: k_harmsum_tma<1><<<grid, 256, 0, s>>>(P, p, tidx0, thr, cands, cap, count, s_out); break;
+        case 2: k_harmsum_tma<2><<<grid, 256, 0, s>>>(P, p, tidx0, thr, cands, cap, count, s_out); break;
+        case 4: k_harmsum_tma<4><<<grid, 256, 0, s>>>(P, p, tidx0, thr, cands, cap, count, s_out); break;
+        case 8: k_harmsum_tma<8><<<grid, 256, 0, s>>>(P, p, tidx0, thr, cands, cap, count, s_out); break;
+        case 16: k_harmsum_tma<16><<<grid, 256, 0, s>>>(P, p, tidx0, thr, cands, cap, count, s_out); break;
         default: return cudaErrorInvalidValue;
     }
     return cudaGetLastError();
