@@ -312,8 +312,8 @@ __device__ __forceinline__ bool mbar_wait_bounded(uint64_t* bar, unsigned long l
 // Incoherent harmonic sum of the whitened spectrum over a tile of 1024 bins.  With
 // H = nharm_max the h-th term of bin k is Pw[(k h + H/2) div H]; over the tile these
 // terms form one contiguous segment per h.  One thread issues 16-byte-aligned TMA bulk
-// copies of the H segments into shared memory (about 8.6 x the tile), all threads wait
-// on the mbarrier (bounded; on expiry the status word is flagged and the tile skipped),
+// copies of the H segments into shared memory (about 8.6 x the tile), warp 0 waits on
+// the mbarrier (bounded; on expiry the status word is flagged and the tile skipped),
 // then each thread sums 4 bins k = k0 + tid + 256 q from shared memory.
 constexpr int kHsTile = 1024;
 
@@ -365,8 +365,15 @@ __global__ void __launch_bounds__(256) k_harmsum_tma(const float* __restrict__ P
             off += b - a;
         }
     }
-    const bool ok = mbar_wait_bounded(&bar, count + 1);
-    if (!ok) return;
+    // one warp waits on the barrier (the others sleep in __syncthreads, issuing nothing);
+    // its acquire plus the CTA barrier make the copied segments visible to all threads
+    __shared__ int s_ok;
+    if (threadIdx.x < 32) {
+        const bool ok = mbar_wait_bounded(&bar, threadIdx.x == 0 ? count + 1 : nullptr);
+        if (threadIdx.x == 0) s_ok = ok;
+    }
+    __syncthreads();
+    if (!s_ok) return;
     const unsigned lane = threadIdx.x & 31u;
     float S[QN][NLEV];
 #pragma unroll
