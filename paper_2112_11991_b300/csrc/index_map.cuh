@@ -99,4 +99,21 @@ __device__ __forceinline__ float gather_sample(const SeriesView& x, int n, int i
     return __half2float(h) * __ldg(x.scale + (idx >> 12));
 }
 
+// Two gathered samples x[i0], x[i1] whose indices are at most a few samples apart:
+// for FP16 storage one scale load serves both unless they straddle a 4096-sample block.
+__device__ __forceinline__ float2 gather_pair(const SeriesView& x, int n, int i0, int i1)
+{
+    if (x.f32) {
+        return make_float2((unsigned)i0 < (unsigned)n ? __ldg(x.f32 + i0) : x.fill,
+                           (unsigned)i1 < (unsigned)n ? __ldg(x.f32 + i1) : x.fill);
+    }
+    const bool in0 = (unsigned)i0 < (unsigned)n, in1 = (unsigned)i1 < (unsigned)n;
+    const int c0 = in0 ? i0 : (in1 ? i1 : 0);
+    const float s0 = __ldg(x.scale + (c0 >> 12));
+    const float s1 = ((i1 >> 12) == (c0 >> 12)) ? s0 : __ldg(x.scale + ((in1 ? i1 : c0) >> 12));
+    const float v0 = in0 ? __half2float(__ushort_as_half(__ldg(x.f16 + i0))) * s0 : x.fill;
+    const float v1 = in1 ? __half2float(__ushort_as_half(__ldg(x.f16 + i1))) * s1 : x.fill;
+    return make_float2(v0, v1);
+}
+
 }  // namespace bps

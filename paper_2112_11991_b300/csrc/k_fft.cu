@@ -332,7 +332,7 @@ __global__ void __launch_bounds__(512, 1) k_pass1(SeriesView x, const Anchor* __
         float2 v[16];
 #pragma unroll
         for (int s = 0; s < 16; ++s)
-            v[s] = make_float2(gather_sample(x, n, id[2 * s]), gather_sample(x, n, id[2 * s + 1]));
+            v[s] = gather_pair(x, n, id[2 * s], id[2 * s + 1]);
         Radix<4>::dft(v);
 #pragma unroll
         for (int s = 0; s < 16; ++s) sm[pad(g + G * (16 * j + s))] = v[Radix<4>::out_pos(s)];
