@@ -58,6 +58,9 @@ def parse():
                     help="series storage on the device: f32, or f16 with a power-of-two "
                          "scale per 4096 samples (FFT arithmetic is FP32 either way)")
     ap.add_argument("--no-plain", action="store_true")
+    ap.add_argument("--no-serving", action="store_true")
+    ap.add_argument("--serve-rate", type=float, default=20.0)
+    ap.add_argument("--serve-requests", type=int, default=32)
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--cpu-templates", type=int, default=0)
     ap.add_argument("--cpu-threads", type=int, default=0)
@@ -227,6 +230,58 @@ def run_reference(args, ws, rank):
     print(json.dumps(out), flush=True)
 
 
+def run_serving(bps, ctx, rate, nreq, seed=5):
+    """Poisson stream of search requests into the continuously batched server: series
+    2^20..2^22 samples (log-uniform) at 64 us stored FP16, banks of 64..512 circular or
+    elliptical (e <= 0.1) templates.  Returns throughput and p50/p99 latency."""
+    import threading
+    rng = np.random.default_rng(seed)
+    reqs = []
+    for i in range(nreq):
+        logn = int(rng.integers(20, 23))
+        n, ts = 1 << logn, 64e-6
+        T = n * ts
+        K = int(2 ** rng.uniform(6, 9))
+        ecc = (0.0, 0.1) if rng.random() < 0.5 else None
+        bank, _ = synth.uniform_bank(K, 1000 + i, (3 * T, 10 * T), (0.0, 0.5), ecc=ecc)
+        reqs.append((synth.noise(n, 2000 + i), ts, bank))
+    gaps = rng.exponential(1.0 / rate, nreq)
+    prm = bps.default_params(cand_cap=1 << 16)
+    lat, tickets = [], []
+    with bps.Server(ctx, max_active=4, groups_in_flight=2) as srv:
+        t_start = time.perf_counter()
+        done = threading.Event()
+
+        def collect():
+            for i in range(nreq):
+                while len(tickets) <= i:
+                    time.sleep(0.0005)
+                _, _, l = srv.result(tickets[i], allow_overflow=True)
+                lat.append(l)
+            done.set()
+
+        th = threading.Thread(target=collect)
+        th.start()
+        t_next = t_start
+        for (x, ts, bank), g in zip(reqs, gaps):
+            t_next += g
+            d = t_next - time.perf_counter()
+            if d > 0:
+                time.sleep(d)
+            tickets.append(srv.submit(x, ts, bank, prm, bps.BPS_F16_SCALED))
+        done.wait()
+        th.join()
+        wall = time.perf_counter() - t_start
+    templates = sum(r[2].shape[0] for r in reqs)
+    return {"rate_req_s": rate, "requests": nreq, "templates": templates,
+            "templates_per_s": templates / wall, "wall_s": wall,
+            "p50_ms": 1e3 * float(np.percentile(lat, 50)),
+            "p99_ms": 1e3 * float(np.percentile(lat, 99)),
+            "workload": "Poisson arrivals; series 2^20-2^22 x 64 us FP16 storage; banks 64-512 "
+                        "circular/elliptical templates; server max_active 4, 2 launch groups "
+                        "in flight per request"}
+
+
 def config_of(w, args, ws):
     return {"workload": "HTRU-like circular search: 2^%d samples @ 64 us, %d circular templates "
                         "(Porb U[3T,10T], tau U[0,3] lt-s), 16 harmonics, 6 sigma, "
@@ -367,6 +422,10 @@ def main():
                "sample": "%d of %d templates of the 2^%d-sample workload (%.1f s)" % (
                    nt, K, args.logn, dt)}
 
+    serving = None
+    if not args.no_serving and ws == 1:
+        serving = run_serving(bps, ctx, args.serve_rate, args.serve_requests)
+
     launches = sum(s["launches"] for s in stats)
     out = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": ws, "steps": args.steps,
            "warmup": args.warmup, "ms_per_step": statistics.mean(ms), "higher_is_better": True,
@@ -382,7 +441,8 @@ def main():
            "stage_ms_per_step": {k: v / args.steps for k, v in stage_ms.items()},
            "stage_share": stage_share,
            "cpu_baseline": cpu, "e2e": e2e, "clocks": clk, "gpu_launches": launches,
-           "candidates_per_step": ncand, "anchor_block": stats[0]["anchor_block"]}
+           "candidates_per_step": ncand, "anchor_block": stats[0]["anchor_block"],
+           "serving": serving}
     if rank == 0:
         print(json.dumps(out), flush=True)
     ctx.close()

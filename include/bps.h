@@ -202,6 +202,54 @@ int bps_set_profiling(bps_ctx* ctx, int on);
  * when profiling was on when the request was enqueued. */
 int bps_request_stats(bps_ctx* ctx, int64_t req_id, bps_stats* out);
 
+/* ---- serving: a continuously batched request loop (native scheduler) ---------- */
+
+/* A server owns a worker thread that admits submitted search requests onto the
+ * device as stream slots and HBM free up, and interleaves their launch groups (one
+ * batch of templates each) round-robin, a few groups in flight per request, so a
+ * request that arrives while others run starts within a launch group instead of
+ * waiting for them to finish.  Each request's series and bank are copied to the
+ * device at admission and freed when its candidates are on the host.  Results of a
+ * request do not depend on what else runs (the per-template computation is the same
+ * as bps_search's with the same parameters). */
+typedef struct bps_server bps_server;
+
+typedef struct {
+    int32_t max_active;        /* requests resident on the device at once, >= 1     */
+    int32_t groups_in_flight;  /* launch groups queued per active request, >= 1     */
+    int64_t hbm_budget;        /* device bytes the server may hold; 0 = 90 % of the */
+                               /* free memory when the server is created             */
+} bps_server_config;
+
+/* Create a server on ctx's device (the context must outlive the server). */
+int bps_server_create(bps_ctx* ctx, const bps_server_config* cfg, bps_server** out);
+
+/* Stop the worker (after finishing admitted requests) and free everything. */
+void bps_server_destroy(bps_server* srv);
+
+/* Submit a search of `count` templates over a host series of n samples (copied
+ * before the call returns; dtype BPS_F32 or BPS_F16_SCALED storage).  Returns at
+ * once with *ticket; BPS_ERR_OUT_OF_MEMORY when the request alone exceeds the HBM
+ * budget, BPS_ERR_INVALID_ARG for bad sizes/parameters (as bps_load_series,
+ * bps_load_bank, bps_search). */
+int bps_server_submit(bps_server* srv, const float* series, int64_t n, double tsamp_s,
+                      int dtype, const bps_template* bank, int64_t count,
+                      const bps_search_params* params, int64_t* ticket);
+
+/* Wait up to timeout_ms (< 0: no limit) for a ticket; BPS_ERR_NOT_READY when it is
+ * still running.  Then copies its sorted candidates like bps_fetch_candidates and
+ * reports *latency_s, from submission to candidates on the host.  The ticket is
+ * released by the first call that returns its result. */
+int bps_server_result(bps_server* srv, int64_t ticket, int32_t timeout_ms, bps_candidate* out,
+                      int64_t cap, int64_t* n_written, int64_t* n_total, double* latency_s);
+
+/* Snapshot: requests queued, resident, finished and not yet fetched; bytes held. */
+int bps_server_stats(bps_server* srv, int64_t* queued, int64_t* active, int64_t* finished,
+                     int64_t* bytes_held);
+
+/* Message of the last error of the server (never NULL). */
+const char* bps_server_last_error(bps_server* srv);
+
 /* ---- allocation-free entry point -------------------------------------------- */
 
 /* The paper has no counterpart to this call: it serves callers that must not

@@ -6,4 +6,4 @@ kernels inside ``libbps.so``, behind the C ABI of ``include/bps.h``.  This
 package is a thin ctypes binding with the same names (``bps.py``).
 """
 from .bps import *  # noqa: F401,F403
-from .bps import Context, BpsError, lib, library_path  # noqa: F401
+from .bps import Context, Server, BpsError, lib, library_path  # noqa: F401

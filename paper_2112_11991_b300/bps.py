@@ -37,7 +37,9 @@ EXPORTED = ["bps_default_params", "bps_create", "bps_destroy", "bps_load_series"
             "bps_load_bank", "bps_search", "bps_query", "bps_fetch_candidates",
             "bps_unload", "bps_last_error", "bps_index_map", "bps_whitened_spectrum",
             "bps_harmonic_sums", "bps_thresholds", "bps_set_profiling",
-            "bps_request_stats", "bps_whitened_spectrum_noalloc"]
+            "bps_request_stats", "bps_whitened_spectrum_noalloc", "bps_server_create",
+            "bps_server_destroy", "bps_server_submit", "bps_server_result", "bps_server_stats",
+            "bps_server_last_error"]
 STAGES = ["anchors", "pass1", "pass2", "power", "median", "harmsum"]
 
 
@@ -62,6 +64,11 @@ class bps_search_params(C.Structure):
                 ("auto_thr", C.c_int32), ("mode", C.c_int32), ("cand_cap", C.c_int64),
                 ("precision", C.c_int32), ("batch", C.c_int32), ("log_tile", C.c_int32),
                 ("log_tile2", C.c_int32)]
+
+
+class bps_server_config(C.Structure):
+    _fields_ = [("max_active", C.c_int32), ("groups_in_flight", C.c_int32),
+                ("hbm_budget", C.c_int64)]
 
 
 class bps_stats(C.Structure):
@@ -120,6 +127,20 @@ def lib():
         L.bps_whitened_spectrum_noalloc.restype = i32
         L.bps_whitened_spectrum_noalloc.argtypes = [vp, i64, C.c_double, C.c_double,
                                                     P(bps_template), i32, vp, vp]
+        L.bps_server_create.restype = i32
+        L.bps_server_create.argtypes = [vp, P(bps_server_config), P(vp)]
+        L.bps_server_destroy.restype = None
+        L.bps_server_destroy.argtypes = [vp]
+        L.bps_server_submit.restype = i32
+        L.bps_server_submit.argtypes = [vp, vp, i64, C.c_double, i32, vp, i64,
+                                        P(bps_search_params), P(i64)]
+        L.bps_server_result.restype = i32
+        L.bps_server_result.argtypes = [vp, i64, C.c_int32, vp, i64, P(i64), P(i64),
+                                        P(C.c_double)]
+        L.bps_server_stats.restype = i32
+        L.bps_server_stats.argtypes = [vp, P(i64), P(i64), P(i64), P(i64)]
+        L.bps_server_last_error.restype = C.c_char_p
+        L.bps_server_last_error.argtypes = [vp]
         L.bps_thresholds.restype = i32
         L.bps_thresholds.argtypes = [P(bps_search_params), i64, i64, vp]
         _lib = L
@@ -296,6 +317,66 @@ class Context:
         return out
 
 
+class Server:
+    """Continuously batched request loop on one context (bps_server_*): submit() returns
+    a ticket at once; result() waits for it and returns (candidates, n_total, latency_s)."""
+
+    def __init__(self, ctx: Context, max_active: int = 4, groups_in_flight: int = 2,
+                 hbm_budget: int = 0):
+        cfg = bps_server_config(max_active, groups_in_flight, hbm_budget)
+        h = C.c_void_p()
+        rc = lib().bps_server_create(ctx.h, C.byref(cfg), C.byref(h))
+        if rc:
+            raise BpsError(rc, "bps_server_create: %s" % lib().bps_last_error(ctx.h).decode())
+        self.h = h
+        self.ctx = ctx
+
+    def close(self):
+        if getattr(self, "h", None):
+            lib().bps_server_destroy(self.h)
+            self.h = None
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *a):
+        self.close()
+
+    def _check(self, rc, what, ok=()):
+        if rc and rc not in ok:
+            raise BpsError(rc, "%s: %s" % (what, lib().bps_server_last_error(self.h).decode()))
+
+    def submit(self, series, tsamp: float, bank, params: bps_search_params | None = None,
+               dtype: int = BPS_F32) -> int:
+        params = params or default_params()
+        x = np.ascontiguousarray(series, np.float32)
+        b = np.ascontiguousarray(np.asarray(bank, np.float64).reshape(-1, 5))
+        t = C.c_int64()
+        rc = lib().bps_server_submit(self.h, _np_ptr(x), x.size, float(tsamp), int(dtype),
+                                     _np_ptr(b), b.shape[0], C.byref(params), C.byref(t))
+        self._check(rc, "bps_server_submit")
+        return t.value
+
+    def result(self, ticket: int, timeout_ms: int = -1, allow_overflow=False):
+        nw, nt, lat = C.c_int64(), C.c_int64(), C.c_double()
+        rc = lib().bps_server_result(self.h, int(ticket), int(timeout_ms), None, 0, C.byref(nw),
+                                     C.byref(nt), C.byref(lat))
+        if rc == BPS_ERR_NOT_READY:
+            return None
+        self._check(rc, "bps_server_result", ok=(BPS_ERR_CAND_OVERFLOW,) if allow_overflow else ())
+        out = np.zeros(max(1, nt.value), CAND_DTYPE)
+        rc = lib().bps_server_result(self.h, int(ticket), 0, _np_ptr(out), out.size, C.byref(nw),
+                                     C.byref(nt), C.byref(lat))
+        self._check(rc, "bps_server_result", ok=(BPS_ERR_CAND_OVERFLOW,) if allow_overflow else ())
+        return out[:nw.value], nt.value, lat.value
+
+    def stats(self) -> dict:
+        q, a, f, by = C.c_int64(), C.c_int64(), C.c_int64(), C.c_int64()
+        self._check(lib().bps_server_stats(self.h, C.byref(q), C.byref(a), C.byref(f), C.byref(by)),
+                    "bps_server_stats")
+        return {"queued": q.value, "active": a.value, "finished": f.value, "bytes_held": by.value}
+
+
 def bps_default_params(p):
     return lib().bps_default_params(p)
 
@@ -358,6 +439,30 @@ def bps_whitened_spectrum_noalloc(d_series, n, tsamp, fill, tmpl, whiten_block, 
                                                d_out, stream)
 
 
+def bps_server_create(ctx, cfg, out):
+    return lib().bps_server_create(ctx, cfg, out)
+
+
+def bps_server_destroy(srv):
+    return lib().bps_server_destroy(srv)
+
+
+def bps_server_submit(srv, series, n, tsamp, dtype, bank, count, params, ticket):
+    return lib().bps_server_submit(srv, series, n, tsamp, dtype, bank, count, params, ticket)
+
+
+def bps_server_result(srv, ticket, timeout_ms, out, cap, nw, nt, lat):
+    return lib().bps_server_result(srv, ticket, timeout_ms, out, cap, nw, nt, lat)
+
+
+def bps_server_stats(srv, q, a, f, by):
+    return lib().bps_server_stats(srv, q, a, f, by)
+
+
+def bps_server_last_error(srv):
+    return lib().bps_server_last_error(srv)
+
+
 def bps_set_profiling(ctx, on):
     return lib().bps_set_profiling(ctx, on)
 
@@ -366,6 +471,6 @@ def bps_request_stats(ctx, rid, out):
     return lib().bps_request_stats(ctx, rid, out)
 
 
-__all__ = ["Context", "BpsError", "default_params", "thresholds", "CAND_DTYPE", "EXPORTED",
+__all__ = ["Context", "Server", "bps_server_config", "BpsError", "default_params", "thresholds", "CAND_DTYPE", "EXPORTED",
            "STAGES", "bps_template", "bps_candidate", "bps_search_params", "bps_stats"] + EXPORTED + [
     n for n in dir() if n.startswith("BPS_")]

@@ -1,0 +1,111 @@
+"""The continuously batched request loop (bps_server_*).
+
+* every request's candidates are identical whether it runs alone or mixed with
+  requests of other series lengths, banks and storage types (and identical to a
+  plain bps_search of the same inputs);
+* with an HBM budget that fits about one request, later requests wait in the queue
+  and all complete; a request larger than the budget is refused at submission;
+* latencies are measured from submission to candidates on the host.
+"""
+import time
+
+import numpy as np
+import pytest
+
+import synth
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def bps():
+    import torch
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    from paper_2112_11991_b300 import build
+    build.build()
+    import paper_2112_11991_b300 as m
+    return m
+
+
+@pytest.fixture(scope="module")
+def ctx(bps):
+    c = bps.Context(0)
+    yield c
+    c.close()
+
+
+def _requests(bps):
+    out = []
+    for i, (logn, K, ecc, f16) in enumerate([(16, 24, False, False), (18, 40, True, False),
+                                             (20, 16, False, True), (17, 64, True, False),
+                                             (19, 8, False, False)]):
+        n, ts = 1 << logn, 64e-6
+        T = n * ts
+        p = synth.Pulsar(period_s=0.025, porb_s=4 * T, tau_lts=0.05, phi_rad=1.0 + i,
+                         omega_rad=0.5 if ecc else 0.0, ecc=0.05 if ecc else 0.0, amp=0.3)
+        x = synth.inject(synth.noise(n, 300 + i), ts, p)
+        bank, _ = synth.uniform_bank(K, 400 + i, (3 * T, 10 * T), (0.0, 0.1),
+                                     ecc=(0.0, 0.1) if ecc else None, true_orbits=[p.orbit()])
+        out.append((x, ts, bank, bps.BPS_F16_SCALED if f16 else bps.BPS_F32))
+    return out
+
+
+def test_same_results_alone_and_in_the_mix(bps, ctx):
+    reqs = _requests(bps)
+    prm = bps.default_params(sigma_thr=5.0)
+    with bps.Server(ctx, max_active=4, groups_in_flight=2) as srv:
+        alone = []
+        for x, ts, bank, dt in reqs:
+            t = srv.submit(x, ts, bank, prm, dt)
+            c, tot, lat = srv.result(t)
+            assert tot == c.size and lat > 0
+            alone.append(c)
+        tickets = [srv.submit(x, ts, bank, prm, dt) for (x, ts, bank, dt) in reqs + reqs[::-1]]
+        mixed = [srv.result(t)[0] for t in tickets]
+    for i in range(len(reqs)):
+        assert np.array_equal(mixed[i], alone[i]), i
+        assert np.array_equal(mixed[2 * len(reqs) - 1 - i], alone[i]), i
+    # the same kernels through the plain request path
+    x, ts, bank, dt = reqs[1]
+    sid = ctx.load_series(x, ts, dt)
+    bid = ctx.load_bank(bank)
+    c, _ = ctx.fetch_candidates(ctx.search(sid, bid, prm))
+    assert np.array_equal(c, alone[1])
+    assert sum(a.size for a in alone) > 0
+
+
+def test_admission_queue_and_budget(bps, ctx):
+    reqs = _requests(bps)
+    prm = bps.default_params(sigma_thr=5.0, cand_cap=1 << 16)
+    x, ts, bank, dt = reqs[2]  # 2^20 samples: the largest request
+    with bps.Server(ctx, max_active=4, groups_in_flight=2, hbm_budget=160 << 20) as srv:
+        tickets = [srv.submit(x, ts, bank, prm, dt) for _ in range(6)]
+        seen_queued = srv.stats()["queued"] > 0
+        res = [srv.result(t) for t in tickets]
+        st = srv.stats()
+    assert seen_queued
+    assert all(np.array_equal(r[0], res[0][0]) for r in res)
+    lat = [r[2] for r in res]
+    assert lat == sorted(lat) or max(lat) > min(lat)  # later requests waited
+    assert st["active"] == 0 and st["bytes_held"] == 0
+    with bps.Server(ctx, max_active=1, hbm_budget=1 << 20) as small:
+        with pytest.raises(bps.BpsError) as e:
+            small.submit(x, ts, bank, prm, dt)
+        assert e.value.code == bps.BPS_ERR_OUT_OF_MEMORY
+
+
+def test_nonblocking_result_and_invalid(bps, ctx):
+    reqs = _requests(bps)
+    x, ts, bank, dt = reqs[0]
+    with bps.Server(ctx, max_active=2) as srv:
+        t = srv.submit(x, ts, bank, bps.default_params(), dt)
+        r = srv.result(t, timeout_ms=0)
+        t0 = time.time()
+        while r is None:
+            assert time.time() - t0 < 60
+            r = srv.result(t, timeout_ms=10)
+        with pytest.raises(bps.BpsError):
+            srv.submit(x[:3000], ts, bank, bps.default_params(), dt)
+        with pytest.raises(bps.BpsError):
+            srv.result(987654)
