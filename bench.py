@@ -319,6 +319,14 @@ def main():
     bid = ctx.load_bank(bank)
     flush = torch.empty(256 << 20, dtype=torch.uint8, device=dev)
 
+    # launch shapes of the fused form chosen by the library's autotuner on 64 templates
+    tuned = None
+    if args.batch == 0 and args.log_tile == 0 and args.log_tile2 == 0:
+        best, ms_t = ctx.autotune(sid, bid, bps.default_params(cand_cap=CAND_CAP),
+                                  sample_templates=min(64, K))
+        tuned = {"log_tile": best.log_tile, "log_tile2": best.log_tile2, "batch": best.batch,
+                 "ms_per_template_sample": ms_t}
+
     def timed_steps(mode, steps, warmup, profile):
         prm = bps.default_params(mode=mode, batch=args.batch if mode == 0 else 0,
                                  cand_cap=CAND_CAP, log_tile=args.log_tile,
@@ -442,7 +450,7 @@ def main():
            "stage_share": stage_share,
            "cpu_baseline": cpu, "e2e": e2e, "clocks": clk, "gpu_launches": launches,
            "candidates_per_step": ncand, "anchor_block": stats[0]["anchor_block"],
-           "serving": serving}
+           "serving": serving, "autotuned": tuned}
     if rank == 0:
         print(json.dumps(out), flush=True)
     ctx.close()

@@ -202,6 +202,16 @@ int bps_set_profiling(bps_ctx* ctx, int on);
  * when profiling was on when the request was enqueued. */
 int bps_request_stats(bps_ctx* ctx, int64_t req_id, bps_stats* out);
 
+/* Autotuner: times every combination of pass-1 tile (2^13, 2^14), pass-2 tile (2^13,
+ * 2^14) and templates per launch (4, 8, 16, 32) on the first sample_templates
+ * templates of the bank over the series (CUDA events, best of two runs), writes the
+ * fastest parameters to *best (other fields copied from *base) and its device time per
+ * template to *best_ms_per_template, and remembers the choice in the context: later
+ * searches of the same series length, mode and harmonic count that leave log_tile,
+ * log_tile2 or batch at 0 use it. */
+int bps_autotune(bps_ctx* ctx, int64_t series_id, int64_t bank_id, const bps_search_params* base,
+                 int64_t sample_templates, bps_search_params* best, double* best_ms_per_template);
+
 /* ---- serving: a continuously batched request loop (native scheduler) ---------- */
 
 /* A server owns a worker thread that admits submitted search requests onto the

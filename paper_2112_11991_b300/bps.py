@@ -39,7 +39,7 @@ EXPORTED = ["bps_default_params", "bps_create", "bps_destroy", "bps_load_series"
             "bps_harmonic_sums", "bps_thresholds", "bps_set_profiling",
             "bps_request_stats", "bps_whitened_spectrum_noalloc", "bps_server_create",
             "bps_server_destroy", "bps_server_submit", "bps_server_result", "bps_server_stats",
-            "bps_server_last_error"]
+            "bps_server_last_error", "bps_autotune"]
 STAGES = ["anchors", "pass1", "pass2", "power", "median", "harmsum"]
 
 
@@ -141,6 +141,9 @@ def lib():
         L.bps_server_stats.argtypes = [vp, P(i64), P(i64), P(i64), P(i64)]
         L.bps_server_last_error.restype = C.c_char_p
         L.bps_server_last_error.argtypes = [vp]
+        L.bps_autotune.restype = i32
+        L.bps_autotune.argtypes = [vp, i64, i64, P(bps_search_params), i64, P(bps_search_params),
+                                   P(C.c_double)]
         L.bps_thresholds.restype = i32
         L.bps_thresholds.argtypes = [P(bps_search_params), i64, i64, vp]
         _lib = L
@@ -276,6 +279,18 @@ class Context:
         if rc and not (rc == BPS_ERR_CAND_OVERFLOW and allow_overflow):
             self._check(rc, "bps_fetch_candidates")
         return out[:nw.value], nt.value
+
+    def autotune(self, series_id: int, bank_id: int, params: bps_search_params | None = None,
+                 sample_templates: int = 64):
+        """Time the launch shapes on a sample of the bank; returns (best params, ms per
+        template).  The context remembers the choice for this series length."""
+        params = params or default_params()
+        best = bps_search_params()
+        ms = C.c_double()
+        rc = lib().bps_autotune(self.h, int(series_id), int(bank_id), C.byref(params),
+                                int(sample_templates), C.byref(best), C.byref(ms))
+        self._check(rc, "bps_autotune")
+        return best, ms.value
 
     def set_profiling(self, on: bool):
         self._check(lib().bps_set_profiling(self.h, int(bool(on))), "bps_set_profiling")
@@ -461,6 +476,10 @@ def bps_server_stats(srv, q, a, f, by):
 
 def bps_server_last_error(srv):
     return lib().bps_server_last_error(srv)
+
+
+def bps_autotune(ctx, sid, bid, base, sample, best, ms):
+    return lib().bps_autotune(ctx, sid, bid, base, sample, best, ms)
 
 
 def bps_set_profiling(ctx, on):

@@ -8,6 +8,7 @@
 #include <cstdarg>
 #include <cstdio>
 #include <cstring>
+#include <array>
 #include <map>
 #include <mutex>
 #include <string>
@@ -72,6 +73,8 @@ struct bps_ctx {
     std::map<FftKey, cufftHandle> ffts;
     float2* tw = nullptr;
     bool profiling = false;
+    // autotuned launch shapes per (log2 n, mode, log2 nharm): tile1, tile2, batch
+    std::map<int, std::array<int, 3>> tuned;
 };
 
 namespace {
@@ -175,7 +178,10 @@ void thresholds(const bps_search_params* pr, int64_t n, int64_t K, double* out)
     for (int L = 0; L < nlev; ++L) out[L] = solve_threshold(1 << L, p);
 }
 
-// Geometry (plan_geometry) + anchor block length (plan_anchor_block).
+int tune_key(int logn, int mode, int lognh) { return (logn << 8) | (mode << 4) | lognh; }
+
+// Geometry (plan_geometry) + anchor block length (plan_anchor_block).  Tiles not given in
+// the parameters come from the context's autotuned entry for this size, else 14 / 13.
 int make_plan(bps_ctx* ctx, const Series& s, const Bank& b, const bps_search_params& pr,
               Plan& p)
 {
@@ -183,7 +189,15 @@ int make_plan(bps_ctx* ctx, const Series& s, const Bank& b, const bps_search_par
     p.logn = ilog2(s.n);
     p.M = s.n / 2;
     p.logM = p.logn - 1;
-    plan_geometry(p, pr.log_tile ? pr.log_tile : 14, pr.log_tile2 ? pr.log_tile2 : 13);
+    int t1 = 14, t2 = 13;
+    if (ctx) {
+        auto it = ctx->tuned.find(tune_key(ilog2(s.n), pr.mode, ilog2(pr.nharm_max)));
+        if (it != ctx->tuned.end()) {
+            t1 = it->second[0];
+            t2 = it->second[1];
+        }
+    }
+    plan_geometry(p, pr.log_tile ? pr.log_tile : t1, pr.log_tile2 ? pr.log_tile2 : t2);
     p.logW = ilog2(pr.whiten_block);
     p.nharm = pr.nharm_max;
     p.lognh = ilog2(pr.nharm_max);
@@ -385,6 +399,10 @@ struct Job {
         thresholds(&prm, s->n, b->K, thr);
         for (int L = 0; L < 5; ++L) th.v[L] = L < p.nlev ? (float)thr[L] : 0.f;
         nt = prm.batch > 0 ? (int)std::min<int64_t>(prm.batch, b->K) : default_batch(p, b->K, mode);
+        if (prm.batch == 0 && ctx) {
+            auto it = ctx->tuned.find(tune_key(p.logn, mode, p.lognh));
+            if (it != ctx->tuned.end()) nt = (int)std::min<int64_t>(it->second[2], b->K);
+        }
         chunk = std::min<int64_t>((int64_t)nt * kAnchorChunk, b->K);
         return ws_alloc(ctx, p, nt, mode, st, w, (int)chunk);
     }
@@ -760,6 +778,73 @@ int bps_request_stats(bps_ctx* ctx, int64_t req_id, bps_stats* out)
         CK(cudaEventElapsedTime(&ms, e.second.first, e.second.second));
         out->stage_ms[e.first] += ms;
     }
+    return BPS_OK;
+}
+
+int bps_autotune(bps_ctx* ctx, int64_t series_id, int64_t bank_id, const bps_search_params* base,
+                 int64_t sample_templates, bps_search_params* best, double* best_ms_per_template)
+{
+    if (!ctx) return BPS_ERR_INVALID_ARG;
+    std::lock_guard<std::recursive_mutex> lk(ctx->mu);
+    Series* s;
+    Bank* b;
+    int rc = lookup(ctx, series_id, bank_id, s, b);
+    if (rc) return rc;
+    if ((rc = check_params(ctx, base, s->n))) return rc;
+    if (!best || sample_templates < 1) return fail(ctx, BPS_ERR_INVALID_ARG, "bad autotune arguments");
+    CK(cudaSetDevice(ctx->device));
+    Bank sub = *b;  // the first sample_templates templates of the bank (same device array)
+    sub.K = std::min<int64_t>(sample_templates, b->K);
+    sub.h.resize((size_t)sub.K);
+    cudaStream_t st = ctx->stream;
+    Cand* cd = nullptr;
+    unsigned long long* cnt = nullptr;
+    CK(cudaMalloc((void**)&cd, sizeof(Cand) * (size_t)base->cand_cap));
+    CK(cudaMalloc((void**)&cnt, 2 * sizeof(unsigned long long)));
+    cudaEvent_t e0, e1;
+    cudaEventCreate(&e0);
+    cudaEventCreate(&e1);
+    const int tiles[2] = {13, 14};
+    const int batches[4] = {4, 8, 16, 32};
+    double best_ms = 1e30;
+    bps_search_params bp = *base;
+    for (int t1 : tiles)
+        for (int t2 : tiles)
+            for (int nb : batches) {
+                if (nb > sub.K) continue;
+                bps_search_params pr = *base;
+                pr.log_tile = t1;
+                pr.log_tile2 = t2;
+                pr.batch = nb;
+                double ms_best = 1e30;
+                for (int rep = 0; rep < 2 && !rc; ++rep) {
+                    cudaMemsetAsync(cnt, 0, 2 * sizeof(unsigned long long), st);
+                    Job job;
+                    if ((rc = job.setup(ctx, s, &sub, pr, st, cd, cnt, pr.cand_cap))) break;
+                    cudaEventRecord(e0, st);
+                    while (!job.done() && !rc) rc = job.issue_batch();
+                    cudaEventRecord(e1, st);
+                    job.release();
+                    cudaEventSynchronize(e1);
+                    float ms = 0.f;
+                    cudaEventElapsedTime(&ms, e0, e1);
+                    ms_best = std::min<double>(ms_best, ms);
+                }
+                if (rc) break;
+                if (ms_best < best_ms) {
+                    best_ms = ms_best;
+                    bp = pr;
+                }
+            }
+    cudaEventDestroy(e0);
+    cudaEventDestroy(e1);
+    cudaFree(cd);
+    cudaFree(cnt);
+    if (rc) return rc;
+    ctx->tuned[tune_key(ilog2(s->n), base->mode, ilog2(base->nharm_max))] = {bp.log_tile, bp.log_tile2,
+                                                                          bp.batch};
+    *best = bp;
+    if (best_ms_per_template) *best_ms_per_template = best_ms / (double)sub.K;
     return BPS_OK;
 }
 

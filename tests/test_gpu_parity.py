@@ -277,3 +277,17 @@ def test_fp16_storage_error_bounded(bps, ctx, orc, w1):
     S = ctx.harmonic_sums(sid, bid, 0, n)
     for L in range(5):
         assert int(np.argmax(S[L])) == int(np.argmax(r["S"][L]))
+
+
+def test_autotune_choice_and_invariance(bps, ctx, w1):
+    n = 1 << 18
+    x = w1.series[:n].copy()
+    sid = ctx.load_series(x, w1.tsamp)
+    bid = ctx.load_bank(w1.bank[:12])
+    ref, _ = ctx.fetch_candidates(ctx.search(sid, bid, bps.default_params(log_tile=14, log_tile2=13,
+                                                                        batch=8)))
+    best, ms = ctx.autotune(sid, bid, bps.default_params(), sample_templates=8)
+    assert best.log_tile in (13, 14) and best.log_tile2 in (13, 14) and best.batch in (4, 8)
+    assert ms > 0
+    got, _ = ctx.fetch_candidates(ctx.search(sid, bid, bps.default_params()))  # uses the choice
+    assert np.array_equal(got, ref)
