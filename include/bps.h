@@ -202,6 +202,19 @@ int bps_set_profiling(bps_ctx* ctx, int on);
  * when profiling was on when the request was enqueued. */
 int bps_request_stats(bps_ctx* ctx, int64_t req_id, bps_stats* out);
 
+/* Candidate distillation (App. A: repeated detections of one candidate are grouped).
+ * Host routine, no device work.  Each candidate's fundamental frequency is
+ * f = bin / (nharm T), T = n_samples t_samp, and its significance the false-alarm
+ * exponent -ln Q(nharm, power) of the Gamma(nharm, 1) tail.  In order of decreasing
+ * significance, each candidate not yet grouped starts a group and takes every other
+ * ungrouped candidate whose f satisfies |q f - p f_0| <= tol_bins/T * max(p, q) for
+ * some 1 <= p, q <= max_ratio (same signal under another template, or a harmonic /
+ * subharmonic of it).  Writes the group leaders (most significant first) to out with
+ * flags = group size, *n_out = number of groups; BPS_ERR_CAND_OVERFLOW if > cap. */
+int bps_distill(const bps_candidate* in, int64_t n_in, int64_t n_samples, double tsamp_s,
+                double tol_bins, int32_t max_ratio, bps_candidate* out, int64_t cap,
+                int64_t* n_out);
+
 /* Autotuner: times every combination of pass-1 tile (2^13, 2^14), pass-2 tile (2^13,
  * 2^14) and templates per launch (4, 8, 16, 32) on the first sample_templates
  * templates of the bank over the series (CUDA events, best of two runs), writes the

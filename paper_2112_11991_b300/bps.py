@@ -39,7 +39,7 @@ EXPORTED = ["bps_default_params", "bps_create", "bps_destroy", "bps_load_series"
             "bps_harmonic_sums", "bps_thresholds", "bps_set_profiling",
             "bps_request_stats", "bps_whitened_spectrum_noalloc", "bps_server_create",
             "bps_server_destroy", "bps_server_submit", "bps_server_result", "bps_server_stats",
-            "bps_server_last_error", "bps_autotune"]
+            "bps_server_last_error", "bps_autotune", "bps_distill"]
 STAGES = ["anchors", "pass1", "pass2", "power", "median", "harmsum"]
 
 
@@ -144,6 +144,9 @@ def lib():
         L.bps_autotune.restype = i32
         L.bps_autotune.argtypes = [vp, i64, i64, P(bps_search_params), i64, P(bps_search_params),
                                    P(C.c_double)]
+        L.bps_distill.restype = i32
+        L.bps_distill.argtypes = [vp, i64, i64, C.c_double, C.c_double, C.c_int32, vp, i64,
+                                  P(i64)]
         L.bps_thresholds.restype = i32
         L.bps_thresholds.argtypes = [P(bps_search_params), i64, i64, vp]
         _lib = L
@@ -170,6 +173,20 @@ def _stream_ptr(stream):
     if isinstance(stream, int):
         return C.c_void_p(stream)
     return C.c_void_p(int(stream.cuda_stream))
+
+
+def distill(cands: np.ndarray, n_samples: int, tsamp: float, tol_bins: float = 1.5,
+            max_ratio: int = 16) -> np.ndarray:
+    """Group repeated / harmonically related detections (bps_distill); returns the group
+    leaders, most significant first, with flags = group size."""
+    c = np.ascontiguousarray(cands, CAND_DTYPE)
+    out = np.zeros(max(1, c.size), CAND_DTYPE)
+    n = C.c_int64()
+    rc = lib().bps_distill(_np_ptr(c), c.size, int(n_samples), float(tsamp), float(tol_bins),
+                           int(max_ratio), _np_ptr(out), out.size, C.byref(n))
+    if rc:
+        raise BpsError(rc, "bps_distill: invalid arguments")
+    return out[:n.value]
 
 
 def thresholds(params: bps_search_params, n_samples: int, n_templates: int) -> np.ndarray:
@@ -482,6 +499,10 @@ def bps_autotune(ctx, sid, bid, base, sample, best, ms):
     return lib().bps_autotune(ctx, sid, bid, base, sample, best, ms)
 
 
+def bps_distill(cin, n_in, n_samples, tsamp, tol, max_ratio, out, cap, n_out):
+    return lib().bps_distill(cin, n_in, n_samples, tsamp, tol, max_ratio, out, cap, n_out)
+
+
 def bps_set_profiling(ctx, on):
     return lib().bps_set_profiling(ctx, on)
 
@@ -490,6 +511,6 @@ def bps_request_stats(ctx, rid, out):
     return lib().bps_request_stats(ctx, rid, out)
 
 
-__all__ = ["Context", "Server", "bps_server_config", "BpsError", "default_params", "thresholds", "CAND_DTYPE", "EXPORTED",
+__all__ = ["Context", "Server", "distill", "bps_server_config", "BpsError", "default_params", "thresholds", "CAND_DTYPE", "EXPORTED",
            "STAGES", "bps_template", "bps_candidate", "bps_search_params", "bps_stats"] + EXPORTED + [
     n for n in dir() if n.startswith("BPS_")]
