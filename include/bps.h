@@ -122,6 +122,12 @@ void bps_destroy(bps_ctx* ctx);
 int bps_load_series(bps_ctx* ctx, const void* data, int64_t n, double tsamp_s,
                     int dtype, int on_device, int64_t* series_id);
 
+/* Replace the samples of a loaded series (same n, tsamp and storage) and recompute
+ * its mean on the device; ordered on the context's stream and synchronous on return.
+ * Searches and graphs that read the series see the new data from then on.  Not for
+ * series that borrow caller device memory (update that memory instead). */
+int bps_series_update(bps_ctx* ctx, int64_t series_id, const void* data, int on_device);
+
 /* Load a template bank (Algorithm 1: "K orbital templates in template bank").
  * t: host array of count templates (copied).  Checks porb > 0, tau >= 0,
  * 0 <= ecc < 1, finite values.  *bank_id receives an id (> 0). */
@@ -201,6 +207,27 @@ int bps_set_profiling(bps_ctx* ctx, int on);
 /* Statistics of a finished request (waits for it).  Stage times are filled only
  * when profiling was on when the request was enqueued. */
 int bps_request_stats(bps_ctx* ctx, int64_t req_id, bps_stats* out);
+
+/* ---- CUDA graphs: many searches, one launch --------------------------------- */
+
+/* Capture the searches of `count` (series, bank) pairs (series of any supported
+ * lengths, each with its own bank) into one CUDA graph: pairs run on up to 4 parallel
+ * branches, each branch with one reusable workspace; each pair has its own candidate
+ * region of params->cand_cap candidates.  Fused mode only (BPS_ERR_UNSUPPORTED
+ * otherwise).  Series and banks must stay loaded while the graph exists; use
+ * bps_series_update to search new data with the same graph.  *graph_id is freed by
+ * bps_unload. */
+int bps_graph_create(bps_ctx* ctx, int64_t count, const int64_t* series_ids,
+                     const int64_t* bank_ids, const bps_search_params* params, int64_t* graph_id);
+
+/* Replay the graph on cuda_stream (NULL = the context's stream).  A replay overwrites
+ * the previous one's candidates: fetch them first. */
+int bps_graph_launch(bps_ctx* ctx, int64_t graph_id, void* cuda_stream);
+
+/* Wait for the last replay and copy pair `pair`'s candidates, sorted by (template_idx,
+ * nharm, bin); return codes as bps_fetch_candidates. */
+int bps_graph_fetch(bps_ctx* ctx, int64_t graph_id, int64_t pair, bps_candidate* out, int64_t cap,
+                    int64_t* n_written, int64_t* n_total);
 
 /* Candidate distillation (App. A: repeated detections of one candidate are grouped).
  * Host routine, no device work.  Each candidate's fundamental frequency is

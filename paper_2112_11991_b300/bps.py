@@ -39,7 +39,8 @@ EXPORTED = ["bps_default_params", "bps_create", "bps_destroy", "bps_load_series"
             "bps_harmonic_sums", "bps_thresholds", "bps_set_profiling",
             "bps_request_stats", "bps_whitened_spectrum_noalloc", "bps_server_create",
             "bps_server_destroy", "bps_server_submit", "bps_server_result", "bps_server_stats",
-            "bps_server_last_error", "bps_autotune", "bps_distill"]
+            "bps_server_last_error", "bps_autotune", "bps_distill", "bps_series_update",
+            "bps_graph_create", "bps_graph_launch", "bps_graph_fetch"]
 STAGES = ["anchors", "pass1", "pass2", "power", "median", "harmsum"]
 
 
@@ -149,6 +150,14 @@ def lib():
                                   P(i64)]
         L.bps_thresholds.restype = i32
         L.bps_thresholds.argtypes = [P(bps_search_params), i64, i64, vp]
+        L.bps_series_update.restype = i32
+        L.bps_series_update.argtypes = [vp, i64, vp, i32]
+        L.bps_graph_create.restype = i32
+        L.bps_graph_create.argtypes = [vp, i64, vp, vp, P(bps_search_params), P(i64)]
+        L.bps_graph_launch.restype = i32
+        L.bps_graph_launch.argtypes = [vp, i64, vp]
+        L.bps_graph_fetch.restype = i32
+        L.bps_graph_fetch.argtypes = [vp, i64, i64, vp, i64, P(i64), P(i64)]
         _lib = L
     return _lib
 
@@ -255,6 +264,20 @@ class Context:
             self.__dict__.setdefault("_borrowed", {})[sid.value] = keep
         return sid.value
 
+    def update_series(self, series_id: int, x):
+        """Replace the samples of a loaded series in place (same length and storage type);
+        ids, banks and graphs that use it stay valid."""
+        if hasattr(x, "data_ptr") and hasattr(x, "is_cuda"):
+            if str(x.dtype) != "torch.float32":
+                raise TypeError("series tensor must be float32")
+            x = x.contiguous()
+            ptr, on_dev, keep = C.c_void_p(x.data_ptr()), int(bool(x.is_cuda)), x
+        else:
+            keep = np.ascontiguousarray(x, np.float32)
+            ptr, on_dev = _np_ptr(keep), 0
+        self._check(lib().bps_series_update(self.h, int(series_id), ptr, on_dev), "bps_series_update")
+        del keep
+
     def load_bank(self, bank) -> int:
         b = np.ascontiguousarray(np.asarray(bank, np.float64).reshape(-1, 5))
         bid = C.c_int64()
@@ -308,6 +331,36 @@ class Context:
                                 int(sample_templates), C.byref(best), C.byref(ms))
         self._check(rc, "bps_autotune")
         return best, ms.value
+
+    # --- CUDA graphs ----------------------------------------------------------------
+    def graph_create(self, pairs, params: bps_search_params | None = None) -> int:
+        """Capture the searches of [(series_id, bank_id), ...] into one CUDA graph."""
+        params = params or default_params()
+        sids = np.array([int(p[0]) for p in pairs], np.int64)
+        bids = np.array([int(p[1]) for p in pairs], np.int64)
+        gid = C.c_int64()
+        rc = lib().bps_graph_create(self.h, sids.size, _np_ptr(sids), _np_ptr(bids),
+                                    C.byref(params), C.byref(gid))
+        self._check(rc, "bps_graph_create")
+        return gid.value
+
+    def graph_launch(self, graph_id: int, stream=None):
+        self._check(lib().bps_graph_launch(self.h, int(graph_id), _stream_ptr(stream)),
+                    "bps_graph_launch")
+
+    def graph_fetch(self, graph_id: int, pair: int, allow_overflow=False):
+        """(candidates of pair `pair` from the last replay, sorted as fetch_candidates; n_total)"""
+        nw, nt = C.c_int64(), C.c_int64()
+        rc = lib().bps_graph_fetch(self.h, int(graph_id), int(pair), None, 0, C.byref(nw),
+                                   C.byref(nt))
+        if rc and not (rc == BPS_ERR_CAND_OVERFLOW and allow_overflow):
+            self._check(rc, "bps_graph_fetch")
+        out = np.zeros(nt.value, CAND_DTYPE)
+        rc = lib().bps_graph_fetch(self.h, int(graph_id), int(pair), _np_ptr(out) if out.size else None,
+                                   out.size, C.byref(nw), C.byref(nt))
+        if rc and not (rc == BPS_ERR_CAND_OVERFLOW and allow_overflow):
+            self._check(rc, "bps_graph_fetch")
+        return out[:nw.value], nt.value
 
     def set_profiling(self, on: bool):
         self._check(lib().bps_set_profiling(self.h, int(bool(on))), "bps_set_profiling")
@@ -505,6 +558,22 @@ def bps_distill(cin, n_in, n_samples, tsamp, tol, max_ratio, out, cap, n_out):
 
 def bps_set_profiling(ctx, on):
     return lib().bps_set_profiling(ctx, on)
+
+
+def bps_series_update(ctx, sid, data, on_device):
+    return lib().bps_series_update(ctx, sid, data, on_device)
+
+
+def bps_graph_create(ctx, count, sids, bids, params, gid):
+    return lib().bps_graph_create(ctx, count, sids, bids, params, gid)
+
+
+def bps_graph_launch(ctx, gid, stream):
+    return lib().bps_graph_launch(ctx, gid, stream)
+
+
+def bps_graph_fetch(ctx, gid, pair, out, cap, nw, nt):
+    return lib().bps_graph_fetch(ctx, gid, pair, out, cap, nw, nt)
 
 
 def bps_request_stats(ctx, rid, out):

@@ -11,6 +11,7 @@
 #include <array>
 #include <map>
 #include <mutex>
+#include <memory>
 #include <string>
 #include <vector>
 
@@ -30,6 +31,8 @@ struct Series {
     uint16_t* f16 = nullptr;
     float* scale = nullptr;
     double mean = 0;
+    double* d_sum = nullptr;  // FP64 sum of the samples (device)
+    float* d_fill = nullptr;  // fill value (the mean) on the device, read by the gather
 };
 
 struct Bank {
@@ -61,6 +64,10 @@ struct FftKey {
 
 }  // namespace
 
+namespace {
+struct GraphObj;
+}
+
 struct bps_ctx {
     int device = 0;
     cudaStream_t stream = nullptr;
@@ -75,6 +82,7 @@ struct bps_ctx {
     bool profiling = false;
     // autotuned launch shapes per (log2 n, mode, log2 nharm): tile1, tile2, batch
     std::map<int, std::array<int, 3>> tuned;
+    std::map<int64_t, GraphObj*> graphs;
 };
 
 namespace {
@@ -231,6 +239,7 @@ SeriesView view_of(const Series& s)
     v.f16 = s.dtype == BPS_F16_SCALED ? s.f16 : nullptr;
     v.scale = s.scale;
     v.fill = (float)s.mean;
+    v.fillp = s.d_fill;
     return v;
 }
 
@@ -256,8 +265,8 @@ size_t align256(size_t v) { return (v + 255) & ~(size_t)255; }
 // Anchors are computed for a chunk of up to kAnchorChunk batches in one launch.
 constexpr int kAnchorChunk = 8;
 
-int ws_alloc(bps_ctx* ctx, const Plan& p, int nt, int mode, cudaStream_t st, Workspace& w,
-             int anchor_templates = 0)
+// Carve a workspace for batches of nt templates (anchors for anchor_templates) out of base.
+size_t ws_carve(const Plan& p, int nt, int mode, int anchor_templates, char* base, Workspace* w)
 {
     const size_t a = align256(sizeof(Anchor) * (size_t)p.nanchor *
                               (anchor_templates > 0 ? anchor_templates : nt));
@@ -265,13 +274,24 @@ int ws_alloc(bps_ctx* ctx, const Plan& p, int nt, int mode, cudaStream_t st, Wor
     const size_t x = mode == BPS_MODE_PLAIN ? align256(sizeof(float) * (size_t)p.n * nt) : 0;
     const size_t pp = align256(sizeof(float) * (size_t)p.M * nt);
     const size_t sc = align256(sizeof(float) * (size_t)(p.M >> p.logW) * nt);
-    CK(cudaMallocAsync((void**)&w.base, a + y + x + pp + sc, st));
-    char* q = w.base;
-    w.anc = (Anchor*)q; q += a;
-    w.Y = (float2*)q; q += y;
-    w.x = x ? (float*)q : nullptr; q += x;
-    w.P = (float*)q; q += pp;
-    w.scale = (float*)q;
+    if (w) {
+        char* q = base;
+        w->base = base;
+        w->anc = (Anchor*)q; q += a;
+        w->Y = (float2*)q; q += y;
+        w->x = x ? (float*)q : nullptr; q += x;
+        w->P = (float*)q; q += pp;
+        w->scale = (float*)q;
+    }
+    return a + y + x + pp + sc;
+}
+
+int ws_alloc(bps_ctx* ctx, const Plan& p, int nt, int mode, cudaStream_t st, Workspace& w,
+             int anchor_templates = 0)
+{
+    char* base = nullptr;
+    CK(cudaMallocAsync((void**)&base, ws_carve(p, nt, mode, anchor_templates, nullptr, nullptr), st));
+    ws_carve(p, nt, mode, anchor_templates, base, &w);
     return BPS_OK;
 }
 
@@ -382,8 +402,12 @@ struct Job {
     bool done() const { return t0 >= b->K; }
 
     // plan, thresholds and workspace (stream-ordered allocation on st)
+    bool owns_ws = true;
+
+    // external: carve the workspace from this buffer (ext_bytes long) instead of allocating
     int setup(bps_ctx* c, const Series* s_, const Bank* b_, const bps_search_params& prm,
-              cudaStream_t stream, Cand* cd, unsigned long long* cnt, int64_t cp)
+              cudaStream_t stream, Cand* cd, unsigned long long* cnt, int64_t cp,
+              char* external = nullptr, size_t ext_bytes = 0)
     {
         ctx = c;
         s = s_;
@@ -404,6 +428,13 @@ struct Job {
             if (it != ctx->tuned.end()) nt = (int)std::min<int64_t>(it->second[2], b->K);
         }
         chunk = std::min<int64_t>((int64_t)nt * kAnchorChunk, b->K);
+        if (external) {
+            if (ws_carve(p, nt, mode, (int)chunk, nullptr, nullptr) > ext_bytes)
+                return fail(ctx, BPS_ERR_INVALID_ARG, "workspace too small");
+            ws_carve(p, nt, mode, (int)chunk, external, &w);
+            owns_ws = false;
+            return BPS_OK;
+        }
         return ws_alloc(ctx, p, nt, mode, st, w, (int)chunk);
     }
 
@@ -440,7 +471,43 @@ struct Job {
         return BPS_OK;
     }
 
-    void release() { if (w.base) cudaFreeAsync(w.base, st); w.base = nullptr; }
+    void release()
+    {
+        if (w.base && owns_ws) cudaFreeAsync(w.base, st);
+        w.base = nullptr;
+    }
+};
+
+// Searches of a list of (series, bank) pairs captured into one CUDA graph: pairs are
+// spread over up to kGraphBranches parallel branches (fork/join events during the
+// capture); the pairs of one branch run in sequence and share its workspace.  Each pair
+// has its own candidate region (cap candidates) and counter.
+constexpr int kGraphBranches = 4;
+
+struct GraphObj {
+    cudaGraph_t graph = nullptr;
+    cudaGraphExec_t exec = nullptr;
+    std::vector<int64_t> series, banks;
+    std::vector<char*> wsbuf;
+    Cand* cands = nullptr;
+    unsigned long long* counts = nullptr;  // 2 per pair: count, status
+    int64_t cap = 0;
+    cudaEvent_t done = nullptr;
+    bool launched = false, fetched = false;
+    std::vector<std::vector<bps_candidate>> results;
+    std::vector<unsigned long long> totals, status;
+    ~GraphObj()
+    {
+        if (done) {
+            cudaEventSynchronize(done);
+            cudaEventDestroy(done);
+        }
+        if (exec) cudaGraphExecDestroy(exec);
+        if (graph) cudaGraphDestroy(graph);
+        for (char* b : wsbuf) cudaFree(b);
+        if (cands) cudaFree(cands);
+        if (counts) cudaFree(counts);
+    }
 };
 
 int lookup(bps_ctx* ctx, int64_t sid, int64_t bid, Series*& s, Bank*& b)
@@ -498,6 +565,8 @@ static void free_series(Series& s)
     if (s.owned && s.f32) cudaFree(s.f32);
     if (s.f16) cudaFree(s.f16);
     if (s.scale) cudaFree(s.scale);
+    if (s.d_sum) cudaFree(s.d_sum);
+    if (s.d_fill) cudaFree(s.d_fill);
     s = Series();
 }
 
@@ -528,6 +597,7 @@ void bps_destroy(bps_ctx* ctx)
         for (auto& s : ctx->series) free_series(s.second);
         for (auto& b : ctx->banks) cudaFree(b.second.d);
         for (auto& f : ctx->ffts) cufftDestroy(f.second);
+        for (auto& gr : ctx->graphs) delete gr.second;
         if (ctx->tw) cudaFree(ctx->tw);
         if (ctx->stream) cudaStreamDestroy(ctx->stream);
     }
@@ -563,13 +633,13 @@ int bps_load_series(bps_ctx* ctx, const void* data, int64_t n, double tsamp_s, i
         tmp = true;
         CK(cudaMemcpyAsync(src, data, sizeof(float) * n, cudaMemcpyHostToDevice, st));
     }
-    double* dsum = nullptr;
-    CK(cudaMallocAsync((void**)&dsum, sizeof(double), st));
-    CK(cudaMemsetAsync(dsum, 0, sizeof(double), st));
-    CK(launch_series_stats(src, n, dsum, st));
+    CK(cudaMalloc((void**)&s.d_sum, sizeof(double)));
+    CK(cudaMalloc((void**)&s.d_fill, sizeof(float)));
+    CK(cudaMemsetAsync(s.d_sum, 0, sizeof(double), st));
+    CK(launch_series_stats(src, n, s.d_sum, st));
+    CK(launch_fill_from_sum(s.d_sum, n, s.d_fill, st));
     double sum = 0;
-    CK(cudaMemcpyAsync(&sum, dsum, sizeof(double), cudaMemcpyDeviceToHost, st));
-    CK(cudaFreeAsync(dsum, st));
+    CK(cudaMemcpyAsync(&sum, s.d_sum, sizeof(double), cudaMemcpyDeviceToHost, st));
     if (dtype == BPS_F32) {
         s.f32 = src;
         s.owned = tmp;
@@ -584,6 +654,42 @@ int bps_load_series(bps_ctx* ctx, const void* data, int64_t n, double tsamp_s, i
     const int64_t id = ctx->next_id++;
     ctx->series[id] = s;
     *series_id = id;
+    return BPS_OK;
+}
+
+int bps_series_update(bps_ctx* ctx, int64_t series_id, const void* data, int on_device)
+{
+    if (!ctx) return BPS_ERR_INVALID_ARG;
+    std::lock_guard<std::recursive_mutex> lk(ctx->mu);
+    auto it = ctx->series.find(series_id);
+    if (it == ctx->series.end() || !data)
+        return fail(ctx, BPS_ERR_INVALID_ARG, "unknown series %lld or null data", (long long)series_id);
+    Series& s = it->second;
+    if (s.dtype == BPS_F32 && !s.owned)
+        return fail(ctx, BPS_ERR_INVALID_ARG, "series %lld borrows caller memory; update that memory instead",
+                    (long long)series_id);
+    CK(cudaSetDevice(ctx->device));
+    cudaStream_t st = ctx->stream;
+    const size_t bytes = sizeof(float) * (size_t)s.n;
+    float* src = nullptr;
+    if (s.dtype == BPS_F32) {
+        src = s.f32;
+        CK(cudaMemcpyAsync(src, data, bytes, on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice, st));
+    } else if (on_device) {
+        src = (float*)data;
+    } else {
+        CK(cudaMallocAsync((void**)&src, bytes, st));
+        CK(cudaMemcpyAsync(src, data, bytes, cudaMemcpyHostToDevice, st));
+    }
+    CK(cudaMemsetAsync(s.d_sum, 0, sizeof(double), st));
+    CK(launch_series_stats(src, s.n, s.d_sum, st));
+    CK(launch_fill_from_sum(s.d_sum, s.n, s.d_fill, st));
+    if (s.dtype != BPS_F32) CK(launch_f16_pack(src, s.n, s.f16, s.scale, st));
+    double sum = 0;
+    CK(cudaMemcpyAsync(&sum, s.d_sum, sizeof(double), cudaMemcpyDeviceToHost, st));
+    if (s.dtype != BPS_F32 && !on_device) CK(cudaFreeAsync(src, st));
+    CK(cudaStreamSynchronize(st));
+    s.mean = sum / (double)s.n;
     return BPS_OK;
 }
 
@@ -730,6 +836,11 @@ int bps_unload(bps_ctx* ctx, int64_t id)
     if (!ctx) return BPS_ERR_INVALID_ARG;
     std::lock_guard<std::recursive_mutex> lk(ctx->mu);
     cudaSetDevice(ctx->device);
+    for (auto& gr : ctx->graphs)
+        for (size_t i = 0; i < gr.second->series.size(); ++i)
+            if (gr.second->series[i] == id || gr.second->banks[i] == id)
+                return fail(ctx, BPS_ERR_INVALID_ARG, "id %lld is captured in graph %lld: unload the graph first",
+                            (long long)id, (long long)gr.first);
     if (ctx->series.count(id)) {
         cudaDeviceSynchronize();
         free_series(ctx->series[id]);
@@ -740,6 +851,11 @@ int bps_unload(bps_ctx* ctx, int64_t id)
         cudaDeviceSynchronize();
         cudaFree(ctx->banks[id].d);
         ctx->banks.erase(id);
+        return BPS_OK;
+    }
+    if (ctx->graphs.count(id)) {
+        delete ctx->graphs[id];
+        ctx->graphs.erase(id);
         return BPS_OK;
     }
     if (ctx->reqs.count(id)) {
@@ -778,6 +894,144 @@ int bps_request_stats(bps_ctx* ctx, int64_t req_id, bps_stats* out)
         CK(cudaEventElapsedTime(&ms, e.second.first, e.second.second));
         out->stage_ms[e.first] += ms;
     }
+    return BPS_OK;
+}
+
+int bps_graph_create(bps_ctx* ctx, int64_t count, const int64_t* series_ids,
+                     const int64_t* bank_ids, const bps_search_params* params, int64_t* graph_id)
+{
+    if (!ctx) return BPS_ERR_INVALID_ARG;
+    std::lock_guard<std::recursive_mutex> lk(ctx->mu);
+    if (count < 1 || !series_ids || !bank_ids || !params || !graph_id)
+        return fail(ctx, BPS_ERR_INVALID_ARG, "bad graph arguments");
+    if (params->mode != BPS_MODE_FUSED)
+        return fail(ctx, BPS_ERR_UNSUPPORTED, "graphs capture the fused form only");
+    CK(cudaSetDevice(ctx->device));
+    CK(set_smem_attributes());
+    const int B = (int)std::min<int64_t>(kGraphBranches, count);
+    std::vector<Series*> ss((size_t)count);
+    std::vector<Bank*> bb((size_t)count);
+    std::vector<size_t> wsb((size_t)B, 0);
+    for (int64_t i = 0; i < count; ++i) {
+        int rc = lookup(ctx, series_ids[i], bank_ids[i], ss[i], bb[i]);
+        if (rc) return rc;
+        if ((rc = check_params(ctx, params, ss[i]->n))) return rc;
+        Plan p;
+        if ((rc = make_plan(ctx, *ss[i], *bb[i], *params, p))) return rc;
+        int nt = params->batch > 0 ? (int)std::min<int64_t>(params->batch, bb[i]->K)
+                                   : default_batch(p, bb[i]->K, params->mode);
+        auto it = ctx->tuned.find(tune_key(p.logn, params->mode, p.lognh));
+        if (params->batch == 0 && it != ctx->tuned.end()) nt = (int)std::min<int64_t>(it->second[2], bb[i]->K);
+        const int64_t chunk = std::min<int64_t>((int64_t)nt * kAnchorChunk, bb[i]->K);
+        wsb[i % B] = std::max(wsb[i % B], ws_carve(p, nt, params->mode, (int)chunk, nullptr, nullptr));
+    }
+    std::unique_ptr<GraphObj> g(new GraphObj());
+    g->series.assign(series_ids, series_ids + count);
+    g->banks.assign(bank_ids, bank_ids + count);
+    g->cap = params->cand_cap;
+    g->wsbuf.assign((size_t)B, nullptr);
+    for (int b = 0; b < B; ++b) CK(cudaMalloc((void**)&g->wsbuf[b], wsb[b]));
+    CK(cudaMalloc((void**)&g->cands, sizeof(Cand) * (size_t)g->cap * count));
+    CK(cudaMalloc((void**)&g->counts, 2 * sizeof(unsigned long long) * count));
+    CK(cudaEventCreateWithFlags(&g->done, cudaEventDisableTiming));
+    cudaStream_t os;
+    std::vector<cudaStream_t> br((size_t)B);
+    CK(cudaStreamCreateWithFlags(&os, cudaStreamNonBlocking));
+    for (auto& x : br) CK(cudaStreamCreateWithFlags(&x, cudaStreamNonBlocking));
+    cudaEvent_t fork;
+    std::vector<cudaEvent_t> join((size_t)B);
+    CK(cudaEventCreateWithFlags(&fork, cudaEventDisableTiming));
+    for (auto& e : join) CK(cudaEventCreateWithFlags(&e, cudaEventDisableTiming));
+    int rc = BPS_OK;
+    cudaError_t ce = cudaStreamBeginCapture(os, cudaStreamCaptureModeThreadLocal);
+    if (ce == cudaSuccess) {
+        cudaMemsetAsync(g->counts, 0, 2 * sizeof(unsigned long long) * count, os);
+        cudaEventRecord(fork, os);
+        for (int b = 0; b < B; ++b) cudaStreamWaitEvent(br[b], fork, 0);
+        for (int64_t i = 0; i < count && !rc; ++i) {
+            Job job;
+            rc = job.setup(ctx, ss[i], bb[i], *params, br[i % B], g->cands + (size_t)i * g->cap,
+                           g->counts + 2 * i, g->cap, g->wsbuf[i % B], wsb[i % B]);
+            while (!rc && !job.done()) rc = job.issue_batch();
+        }
+        for (int b = 0; b < B; ++b) {
+            cudaEventRecord(join[b], br[b]);
+            cudaStreamWaitEvent(os, join[b], 0);
+        }
+        ce = cudaStreamEndCapture(os, &g->graph);
+        if (ce == cudaSuccess && !rc) ce = cudaGraphInstantiate(&g->exec, g->graph, 0);
+    }
+    cudaEventDestroy(fork);
+    for (auto e : join) cudaEventDestroy(e);
+    for (auto x : br) cudaStreamDestroy(x);
+    cudaStreamDestroy(os);
+    if (rc) return rc;
+    if (ce != cudaSuccess) return fail(ctx, BPS_ERR_CUDA, "graph capture: %s", cudaGetErrorString(ce));
+    const int64_t id = ctx->next_id++;
+    ctx->graphs[id] = g.release();
+    *graph_id = id;
+    return BPS_OK;
+}
+
+int bps_graph_launch(bps_ctx* ctx, int64_t graph_id, void* cuda_stream)
+{
+    if (!ctx) return BPS_ERR_INVALID_ARG;
+    std::lock_guard<std::recursive_mutex> lk(ctx->mu);
+    auto it = ctx->graphs.find(graph_id);
+    if (it == ctx->graphs.end()) return fail(ctx, BPS_ERR_INVALID_ARG, "unknown graph %lld", (long long)graph_id);
+    GraphObj& g = *it->second;
+    CK(cudaSetDevice(ctx->device));
+    cudaStream_t st = cuda_stream ? (cudaStream_t)cuda_stream : ctx->stream;
+    CK(cudaGraphLaunch(g.exec, st));
+    CK(cudaEventRecord(g.done, st));
+    g.launched = true;
+    g.fetched = false;
+    return BPS_OK;
+}
+
+int bps_graph_fetch(bps_ctx* ctx, int64_t graph_id, int64_t pair, bps_candidate* out, int64_t cap,
+                    int64_t* n_written, int64_t* n_total)
+{
+    if (!ctx) return BPS_ERR_INVALID_ARG;
+    std::lock_guard<std::recursive_mutex> lk(ctx->mu);
+    auto it = ctx->graphs.find(graph_id);
+    if (it == ctx->graphs.end()) return fail(ctx, BPS_ERR_INVALID_ARG, "unknown graph %lld", (long long)graph_id);
+    GraphObj& g = *it->second;
+    const int64_t np = (int64_t)g.series.size();
+    if (pair < 0 || pair >= np || !g.launched) return fail(ctx, BPS_ERR_INVALID_ARG, "bad pair or graph not launched");
+    CK(cudaSetDevice(ctx->device));
+    if (!g.fetched) {
+        CK(cudaEventSynchronize(g.done));
+        std::vector<unsigned long long> cs(2 * (size_t)np);
+        CK(cudaMemcpy(cs.data(), g.counts, sizeof(unsigned long long) * cs.size(), cudaMemcpyDeviceToHost));
+        g.results.assign((size_t)np, {});
+        g.totals.assign((size_t)np, 0);
+        g.status.assign((size_t)np, 0);
+        for (int64_t i = 0; i < np; ++i) {
+            g.totals[i] = cs[2 * i];
+            g.status[i] = cs[2 * i + 1];
+            const int64_t kept = std::min<int64_t>((int64_t)cs[2 * i], g.cap);
+            g.results[i].resize((size_t)kept);
+            if (kept)
+                CK(cudaMemcpy(g.results[i].data(), g.cands + (size_t)i * g.cap, sizeof(Cand) * kept,
+                              cudaMemcpyDeviceToHost));
+            std::sort(g.results[i].begin(), g.results[i].end(), [](const bps_candidate& a, const bps_candidate& b) {
+                if (a.template_idx != b.template_idx) return a.template_idx < b.template_idx;
+                if (a.nharm != b.nharm) return a.nharm < b.nharm;
+                return a.bin < b.bin;
+            });
+        }
+        g.fetched = true;
+    }
+    const auto& r = g.results[pair];
+    const int64_t nw = std::min<int64_t>(cap, (int64_t)r.size());
+    if (out && nw > 0) std::memcpy(out, r.data(), sizeof(bps_candidate) * nw);
+    if (n_written) *n_written = out ? nw : 0;
+    if (n_total) *n_total = (int64_t)g.totals[pair];
+    if (g.status[pair] & 1ull) return fail(ctx, BPS_ERR_TIMEOUT, "a bounded device wait expired");
+    if ((int64_t)g.totals[pair] > g.cap)
+        return fail(ctx, BPS_ERR_CAND_OVERFLOW, "pair %lld: %llu candidates, capacity %lld",
+                    (long long)pair, g.totals[pair], (long long)g.cap);
     return BPS_OK;
 }
 

@@ -111,6 +111,7 @@ struct SeriesView {
     const uint16_t* f16;       // FP16 samples (or nullptr)
     const float* scale;        // per-4096-sample scale for FP16
     float fill;                // mean of the series (value for out-of-range samples)
+    const float* fillp;        // device copy of the fill value (used when non-null)
 };
 
 // Launchers (stream-ordered, return cudaGetLastError()).
@@ -123,6 +124,7 @@ cudaError_t launch_index_map(const Anchor* anc, const Plan& p, int32_t* idx,
                              unsigned long long* n_precise, cudaStream_t s);
 cudaError_t launch_resample(const SeriesView& x, const Anchor* anc, int nt, const Plan& p,
                             float* out, cudaStream_t s);
+cudaError_t set_smem_attributes();
 cudaError_t launch_pass1(const SeriesView& x, const Anchor* anc, int nt, const Plan& p,
                          const float2* tw, float2* Y, cudaStream_t s);
 cudaError_t launch_pass2(const float2* Y, int nt, const Plan& p, const float2* tw,
@@ -141,6 +143,8 @@ cudaError_t launch_harmsum(const float* P, const float* scale, int nt, int64_t t
                            const Plan& p, const Thr& thr, Cand* cands, int64_t cap,
                            unsigned long long* count, float* s_out, cudaStream_t s);
 cudaError_t launch_series_stats(const float* x, int64_t n, double* sum, cudaStream_t s);
+// fill = (float)(sum / n) on the device
+cudaError_t launch_fill_from_sum(const double* sum, int64_t n, float* fill, cudaStream_t s);
 cudaError_t launch_f16_pack(const float* x, int64_t n, uint16_t* h, float* scale,
                             cudaStream_t s);
 

@@ -140,6 +140,7 @@ extern "C" int bps_whitened_spectrum_noalloc(const float* d_series, int64_t n, d
     v.f16 = nullptr;
     v.scale = nullptr;
     v.fill = (float)fill;
+    v.fillp = nullptr;
     if (launch_twiddle_init(tw, st) != cudaSuccess) return BPS_ERR_CUDA;
     k_store_template<<<1, 1, 0, st>>>(tv, dt);
     if (cudaGetLastError() != cudaSuccess) return BPS_ERR_CUDA;

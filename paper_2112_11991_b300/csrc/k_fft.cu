@@ -17,6 +17,7 @@
 // radix-8/4/2 stage; each thread keeps its EPT = 32 elements in registers across
 // the barrier between the read and the write of a stage.
 #include <cmath>
+#include <mutex>
 
 #include "bps_internal.cuh"
 #include "index_map.cuh"
@@ -475,6 +476,24 @@ size_t tile_smem(int logt) { return (size_t)(((1 << logt) + ((1 << logt) >> 4) +
 
 }  // namespace
 
+// Large dynamic shared memory for the FFT passes, set once per device (a host-side
+// function attribute, so it is also safe to call while a stream is being captured).
+cudaError_t set_smem_attributes()
+{
+    static std::mutex mu;
+    static bool done[64] = {};
+    int dev = 0;
+    cudaError_t e = cudaGetDevice(&dev);
+    if (e != cudaSuccess || dev < 0 || dev >= 64) return e != cudaSuccess ? e : cudaErrorInvalidDevice;
+    std::lock_guard<std::mutex> lk(mu);
+    if (done[dev]) return cudaSuccess;
+    e = cudaFuncSetAttribute(k_pass1, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)tile_smem(kLogTile));
+    if (e == cudaSuccess)
+        e = cudaFuncSetAttribute(k_pass2, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)tile_smem(kLogTile));
+    if (e == cudaSuccess) done[dev] = true;
+    return e;
+}
+
 cudaError_t launch_twiddle_init(float2* tw, cudaStream_t s)
 {
     k_twiddle_init<<<kTwiddleN / 256, 256, 0, s>>>(tw);
@@ -485,8 +504,7 @@ cudaError_t launch_pass1(const SeriesView& x, const Anchor* anc, int nt, const P
                          const float2* tw, float2* Y, cudaStream_t s)
 {
     const int logt = p.logR + p.logG;
-    cudaError_t e = cudaFuncSetAttribute(k_pass1, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                         (int)tile_smem(kLogTile));
+    cudaError_t e = set_smem_attributes();
     if (e != cudaSuccess) return e;
     dim3 grid((unsigned)(1 << (p.logC - p.logG)), (unsigned)nt);
     k_pass1<<<grid, (1 << logt) / kEPT, tile_smem(logt), s>>>(x, anc, p, tw, Y);
@@ -497,8 +515,7 @@ cudaError_t launch_pass2(const float2* Y, int nt, const Plan& p, const float2* t
                          cudaStream_t s)
 {
     const int logt = p.logNP + 1 + p.logC;
-    cudaError_t e = cudaFuncSetAttribute(k_pass2, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                         (int)tile_smem(kLogTile));
+    cudaError_t e = set_smem_attributes();
     if (e != cudaSuccess) return e;
     dim3 grid((unsigned)(1 << (p.logR - 1 - p.logNP)), (unsigned)nt);
     k_pass2<<<grid, (1 << logt) / kEPT, tile_smem(logt), s>>>(Y, p, tw, P);

@@ -179,7 +179,18 @@ __global__ void k_f16_pack(const float* __restrict__ x, int64_t n, uint16_t* __r
         if (base + i < n) h[base + i] = __half_as_ushort(__float2half_rn(x[base + i] * inv));
 }
 
+__global__ void k_fill_from_sum(const double* __restrict__ sum, int64_t n, float* __restrict__ fill)
+{
+    if (threadIdx.x == 0 && blockIdx.x == 0) *fill = (float)(*sum / (double)n);
+}
+
 }  // namespace
+
+cudaError_t launch_fill_from_sum(const double* sum, int64_t n, float* fill, cudaStream_t s)
+{
+    k_fill_from_sum<<<1, 32, 0, s>>>(sum, n, fill);
+    return cudaGetLastError();
+}
 
 cudaError_t launch_anchors(const DevTemplate* bank, int64_t t0, int nt, const Plan& p,
                            Anchor* out, cudaStream_t s)
