@@ -90,10 +90,17 @@ __device__ __forceinline__ Anchor load_anchor(const Anchor* __restrict__ anc, in
     return anc[b];
 }
 
+// Kernels that gather call this once at entry: the fill value comes from the device copy
+// when there is one (series updated in place, graphs), so the gathers below read a register.
+__device__ __forceinline__ void resolve_fill(SeriesView& x)
+{
+    if (x.fillp) x.fill = __ldg(x.fillp);
+}
+
 // Gathered sample x[idx] (the series mean outside [0, n)), FP32 or FP16+scale.
 __device__ __forceinline__ float gather_sample(const SeriesView& x, int n, int idx)
 {
-    if ((unsigned)idx >= (unsigned)n) return x.fillp ? __ldg(x.fillp) : x.fill;
+    if ((unsigned)idx >= (unsigned)n) return x.fill;
     if (x.f32) return __ldg(x.f32 + idx);
     const __half h = __ushort_as_half(__ldg(x.f16 + idx));
     return __half2float(h) * __ldg(x.scale + (idx >> 12));
@@ -103,14 +110,16 @@ __device__ __forceinline__ float gather_sample(const SeriesView& x, int n, int i
 // for FP16 storage one scale load serves both unless they straddle a 4096-sample block.
 __device__ __forceinline__ float2 gather_pair(const SeriesView& x, int n, int i0, int i1)
 {
+    if (x.f32) {
+        return make_float2((unsigned)i0 < (unsigned)n ? __ldg(x.f32 + i0) : x.fill,
+                           (unsigned)i1 < (unsigned)n ? __ldg(x.f32 + i1) : x.fill);
+    }
     const bool in0 = (unsigned)i0 < (unsigned)n, in1 = (unsigned)i1 < (unsigned)n;
-    const float fill = (in0 && in1) ? 0.f : (x.fillp ? __ldg(x.fillp) : x.fill);
-    if (x.f32) return make_float2(in0 ? __ldg(x.f32 + i0) : fill, in1 ? __ldg(x.f32 + i1) : fill);
     const int c0 = in0 ? i0 : (in1 ? i1 : 0);
     const float s0 = __ldg(x.scale + (c0 >> 12));
     const float s1 = ((i1 >> 12) == (c0 >> 12)) ? s0 : __ldg(x.scale + ((in1 ? i1 : c0) >> 12));
-    const float v0 = in0 ? __half2float(__ushort_as_half(__ldg(x.f16 + i0))) * s0 : fill;
-    const float v1 = in1 ? __half2float(__ushort_as_half(__ldg(x.f16 + i1))) * s1 : fill;
+    const float v0 = in0 ? __half2float(__ushort_as_half(__ldg(x.f16 + i0))) * s0 : x.fill;
+    const float v1 = in1 ? __half2float(__ushort_as_half(__ldg(x.f16 + i1))) * s1 : x.fill;
     return make_float2(v0, v1);
 }
 

@@ -280,6 +280,7 @@ __global__ void __launch_bounds__(512, 1) k_pass1(SeriesView x, const Anchor* __
                                                   float2* __restrict__ Y)
 {
     extern __shared__ float2 sm[];
+    resolve_fill(x);
     const int tl = blockIdx.y;
     const int logG = p.logG;
     const int G = 1 << logG;

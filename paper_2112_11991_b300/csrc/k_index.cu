@@ -123,6 +123,7 @@ __global__ void k_resample(SeriesView x, const Anchor* __restrict__ anc, Plan p,
     const int tl = blockIdx.y;
     const int64_t m = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     if (m >= p.n) return;
+    resolve_fill(x);
     const Anchor* at = anc + (int64_t)tl * p.nanchor;
     const int64_t b = anchor_of(m, p.logB);
     const Anchor a = at[b];
