@@ -246,7 +246,7 @@ SeriesView view_of(const Series& s)
 int default_batch(const Plan& p, int64_t K, int mode)
 {
     if (mode == BPS_MODE_PLAIN) return 1;
-    int64_t nt = std::max<int64_t>(1, (1ll << 25) / p.M);
+    int64_t nt = std::max<int64_t>(1, (1ll << 27) / p.M);
     nt = std::min<int64_t>(nt, 64);
     return (int)std::min<int64_t>(nt, std::max<int64_t>(K, 1));
 }
@@ -1059,7 +1059,7 @@ int bps_autotune(bps_ctx* ctx, int64_t series_id, int64_t bank_id, const bps_sea
     cudaEventCreate(&e0);
     cudaEventCreate(&e1);
     const int tiles[2] = {13, 14};
-    const int batches[4] = {4, 8, 16, 32};
+    const int batches[4] = {8, 16, 32, 64};
     double best_ms = 1e30;
     bps_search_params bp = *base;
     for (int t1 : tiles)

@@ -10,7 +10,11 @@
 // (k h' (H/n) + H/2) div H, so S_1 = F_H and S_{2n} = S_n + sum over odd h of
 // F_{h H / (2n)}: 16 loads per bin for all five levels.  Threshold (Sec. 2.1)
 // and warp-ballot compaction: one atomic per warp and level with hits.
+#include <algorithm>
+#include <climits>
 #include <cmath>
+#include <cstdint>
+#include <mutex>
 
 #include "bps_internal.cuh"
 
@@ -165,93 +169,6 @@ __global__ void __launch_bounds__(256) k_median_warp(float* __restrict__ P, Plan
     if (lane == 0) scale[(int64_t)tl * nblk + blk] = sc;
 }
 
-// Incoherent harmonic sum of the whitened spectrum.  With H = nharm_max the h-th
-// term of bin k is Pw[(k h + H/2) div H].  A warp covers 32 QN consecutive bins as
-// k = k_w + lane + 32 q (q < QN), so for each h the QN terms sit at
-// ((k_w + lane) h + H/2) div H + 32 q h / H: one index per h plus compile-time
-// offsets, QN H independent coalesced loads per thread.
-template <int NH, int QN>
-__global__ void __launch_bounds__(256) k_harmsum_direct(const float* __restrict__ Pw, Plan p,
-                                                        int64_t tidx0, Thr thr,
-                                                        Cand* __restrict__ cands, int64_t cap,
-                                                        unsigned long long* __restrict__ count,
-                                                        float* __restrict__ s_out)
-{
-    constexpr int LOGNH = (NH == 1) ? 0 : (NH == 2) ? 1 : (NH == 4) ? 2 : (NH == 8) ? 3 : 4;
-    constexpr int NLEV = LOGNH + 1;
-    const int tl = blockIdx.y;
-    const unsigned lane = threadIdx.x & 31u;
-    const int kb = (blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5)) * (32 * QN) + (int)lane;
-    const float* Pt = Pw + (int64_t)tl * p.M;
-    float S[QN][NLEV];
-    {
-        float F[QN][NH];
-#pragma unroll
-        for (int h = 1; h <= NH; ++h) {
-            const float* ph = Pt + ((kb * h + (NH >> 1)) >> LOGNH);  // kb*h < 2^28
-#pragma unroll
-            for (int q = 0; q < QN; ++q) F[q][h - 1] = __ldg(ph + ((32 * q * h) >> LOGNH));
-        }
-#pragma unroll
-        for (int q = 0; q < QN; ++q) {
-            float s = F[q][NH - 1];
-            S[q][0] = s;
-#pragma unroll
-            for (int L = 1; L < NLEV; ++L) {
-                const int n = 1 << L;
-                const int step = NH / n;
-#pragma unroll
-                for (int h = 1; h <= n; h += 2) s += F[q][h * step - 1];
-                S[q][L] = s;
-            }
-        }
-    }
-    if (s_out) {
-#pragma unroll
-        for (int q = 0; q < QN; ++q) {
-            const int k = kb + 32 * q;
-#pragma unroll
-            for (int L = 0; L < NLEV; ++L)
-                s_out[((int64_t)tl * NLEV + L) * p.M + k] = (k >= 1) ? S[q][L] : 0.f;
-        }
-    }
-    // threshold: one warp vote for all levels and bins first (detections are rare)
-    bool any = false;
-#pragma unroll
-    for (int q = 0; q < QN; ++q)
-#pragma unroll
-        for (int L = 0; L < NLEV; ++L) any |= (S[q][L] >= thr.v[L]) && (kb + 32 * q >= 1);
-    if (!__any_sync(0xffffffffu, any)) return;
-#pragma unroll
-    for (int q = 0; q < QN; ++q) {
-        const int k = kb + 32 * q;
-        const bool valid = k >= 1;
-#pragma unroll
-        for (int L = 0; L < NLEV; ++L) {
-            const bool hit = valid && (S[q][L] >= thr.v[L]);
-            const unsigned m = __ballot_sync(0xffffffffu, hit);
-            if (m) {
-                const int leader = __ffs(m) - 1;
-                unsigned long long b0 = 0;
-                if ((int)lane == leader) b0 = atomicAdd(count, (unsigned long long)__popc(m));
-                b0 = __shfl_sync(0xffffffffu, b0, leader);
-                if (hit) {
-                    const unsigned long long pos = b0 + __popc(m & ((1u << lane) - 1u));
-                    if ((int64_t)pos < cap) {
-                        Cand c;
-                        c.tidx = (uint32_t)(tidx0 + tl);
-                        c.nharm = (uint16_t)(1 << L);
-                        c.flags = 0;
-                        c.bin = (uint32_t)k;
-                        c.power = S[q][L];
-                        cands[pos] = c;
-                    }
-                }
-            }
-        }
-    }
-}
-
 // ---- TMA bulk copies into shared memory, completed on an mbarrier (inline PTX) ----
 __device__ __forceinline__ uint32_t smem_u32(const void* p)
 {
@@ -295,142 +212,199 @@ __device__ __forceinline__ bool mbar_try_wait(uint64_t* bar, uint32_t phase)
     return ok != 0;
 }
 
-// Bounded wait for phase 0 of the barrier: false (and error flag set) after the limit.
 constexpr int kWaitLimit = 1 << 22;
 
-__device__ __forceinline__ bool mbar_wait_bounded(uint64_t* bar, unsigned long long* status)
+// Bounded wait for the given phase parity of an mbarrier; false after the limit.
+__device__ __forceinline__ bool mbar_wait_parity(uint64_t* bar, uint32_t parity)
 {
     for (int it = 0; it < kWaitLimit; ++it)
-        if (mbar_try_wait(bar, 0)) return true;
-    if (status) atomicOr(status, 1ull);  // BPS_ERR_TIMEOUT reported by the host
-    // the copies may still be in flight: give them a second bounded wait before exiting
-    for (int it = 0; it < kWaitLimit; ++it)
-        if (mbar_try_wait(bar, 0)) break;
+        if (mbar_try_wait(bar, parity)) return true;
     return false;
 }
 
-// Incoherent harmonic sum of the whitened spectrum over a tile of 1024 bins.  With
-// H = nharm_max the h-th term of bin k is Pw[(k h + H/2) div H]; over the tile these
-// terms form one contiguous segment per h.  One thread issues 16-byte-aligned TMA bulk
-// copies of the H segments into shared memory (about 8.6 x the tile), warp 0 waits on
-// the mbarrier (bounded; on expiry the status word is flagged and the tile skipped),
-// then each thread sums 4 bins k = k0 + tid + 256 q from shared memory.
+// Arrive on an mbarrier (release; one arrival).
+__device__ __forceinline__ void mbar_arrive(uint64_t* bar)
+{
+    asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(smem_u32(bar)) : "memory");
+}
+
+// Incoherent harmonic sum of the whitened spectrum over tiles of kHsTile = 1024 bins.
+// With H = nharm_max the h-th term of bin k is Pw[(k h + H/2) div H].  For a tile
+// starting at k0 (a multiple of 1024) and k = k0 + t + 256 q (thread t < 256, q < 4):
+//   (k h + H/2) div H = k0 h / H + 256 q h / H + (t h + H/2) div H,
+// since k0 h / H and 256 q h / H are whole.  So the terms of h form the segment
+// Pw[k0 h / H, k0 h / H + len_h) with len_h independent of k0, the segment's place in
+// shared memory is the same for every tile, and a thread's h-th address is a per-thread
+// register plus a compile-time offset: 16 shared loads and no index arithmetic per bin.
+// Warp-specialised pipeline: one producer warp copies the H segments of a tile into a
+// ring of kHsStages stages (16-byte-aligned TMA bulk copies, one per lane, completed on
+// the stage's "full" mbarrier); 8 consumer warps sum, threshold and compact, then release
+// the stage on its "empty" mbarrier.  CTAs are persistent over tiles j = blockIdx.x +
+// i gridDim.x.  Every wait is bounded: on expiry the status word is flagged (reported as
+// BPS_ERR_TIMEOUT) and the warp leaves after a bounded drain of its copies in flight.
 constexpr int kHsTile = 1024;
+constexpr int kHsConsumerWarps = 8;
+constexpr int kHsThreads = 32 * (kHsConsumerWarps + 1);
+constexpr int kHsQN = kHsTile / (32 * kHsConsumerWarps);
+constexpr int kHsStages = 3;
+constexpr int kHsHeader = 128;  // bytes: full and empty barriers
 
 template <int NH>
-__global__ void __launch_bounds__(256) k_harmsum_tma(const float* __restrict__ Pw, Plan p,
-                                                     int64_t tidx0, Thr thr,
-                                                     Cand* __restrict__ cands, int64_t cap,
-                                                     unsigned long long* __restrict__ count,
-                                                     float* __restrict__ s_out)
+struct HsGeom {
+    static constexpr int LOGNH = (NH == 1) ? 0 : (NH == 2) ? 1 : (NH == 4) ? 2 : (NH == 8) ? 3 : 4;
+    // segment length (floats, multiple of 4) and offset of harmonic h within a stage
+    __host__ __device__ static constexpr int len(int h) { return ((((kHsTile - 1) * h + (NH >> 1)) >> LOGNH) + 4) & ~3; }
+    __host__ __device__ static constexpr int off(int h) { return h <= 1 ? 0 : off(h - 1) + len(h - 1); }
+    static constexpr int SEG = off(NH + 1);  // floats per stage
+    static constexpr uint32_t BYTES = (uint32_t)SEG * 4u;
+    static constexpr size_t SMEM = kHsHeader + (size_t)kHsStages * SEG * sizeof(float);
+};
+
+template <int NH>
+__global__ void __launch_bounds__(kHsThreads, 2) k_harmsum(const float* __restrict__ Pw, Plan p,
+                                                        int64_t tidx0, Thr thr,
+                                                        Cand* __restrict__ cands, int64_t cap,
+                                                        unsigned long long* __restrict__ count,
+                                                        float* __restrict__ s_out, int ntiles)
 {
-    constexpr int LOGNH = (NH == 1) ? 0 : (NH == 2) ? 1 : (NH == 4) ? 2 : (NH == 8) ? 3 : 4;
+    using Gm = HsGeom<NH>;
+    constexpr int LOGNH = Gm::LOGNH;
     constexpr int NLEV = LOGNH + 1;
-    constexpr int QN = kHsTile / 256;
-    constexpr int SEG = kHsTile * (NH + 1) / 2 + 8 * NH;
-    __shared__ __align__(128) float seg[SEG];
-    __shared__ __align__(8) uint64_t bar;
-    const int tl = blockIdx.y;
-    const int k0 = blockIdx.x * kHsTile;
-    const float* Pt = Pw + (int64_t)tl * p.M;
-    if (threadIdx.x == 0) mbar_init(&bar, 1);
-    __syncthreads();
-    if (threadIdx.x == 0) {
-        uint32_t total = 0;
-#pragma unroll
-        for (int h = 1; h <= NH; ++h) {
-            const int a = ((k0 * h + (NH >> 1)) >> LOGNH) & ~3;
-            const int b = ((((k0 + kHsTile - 1) * h + (NH >> 1)) >> LOGNH) + 4) & ~3;
-            total += (uint32_t)(b - a) * 4u;
-        }
-        mbar_expect_tx(&bar, total);
-        int off = 0;
-#pragma unroll
-        for (int h = 1; h <= NH; ++h) {
-            const int a = ((k0 * h + (NH >> 1)) >> LOGNH) & ~3;
-            const int b = ((((k0 + kHsTile - 1) * h + (NH >> 1)) >> LOGNH) + 4) & ~3;
-            tma_load_1d(seg + off, Pt + a, (uint32_t)(b - a) * 4u, &bar);
-            off += b - a;
-        }
-    }
-    // per-thread base index of each segment (computed while the copies fly)
-    int base[NH];
-    {
-        int off = 0;
-#pragma unroll
-        for (int h = 1; h <= NH; ++h) {
-            const int a = ((k0 * h + (NH >> 1)) >> LOGNH) & ~3;
-            const int b = ((((k0 + kHsTile - 1) * h + (NH >> 1)) >> LOGNH) + 4) & ~3;
-            base[h - 1] = off + ((((k0 + (int)threadIdx.x) * h + (NH >> 1)) >> LOGNH) - a);
-            off += b - a;
-        }
-    }
-    // one warp waits on the barrier (the others sleep in __syncthreads, issuing nothing);
-    // its acquire plus the CTA barrier make the copied segments visible to all threads
-    __shared__ int s_ok;
-    if (threadIdx.x < 32) {
-        const bool ok = mbar_wait_bounded(&bar, threadIdx.x == 0 ? count + 1 : nullptr);
-        if (threadIdx.x == 0) s_ok = ok;
-    }
-    __syncthreads();
-    if (!s_ok) return;
+    constexpr int QN = kHsQN;
+    constexpr int CT = 32 * kHsConsumerWarps;  // consumer threads
+    constexpr int SEG = Gm::SEG;
+    extern __shared__ __align__(128) unsigned char hsm[];
+    uint64_t* full = reinterpret_cast<uint64_t*>(hsm);
+    uint64_t* empty = full + kHsStages;
+    float* seg = reinterpret_cast<float*>(hsm + kHsHeader);
+    const int logtpt = p.logM - 10;  // tiles per template = M / 1024
+    const int G = gridDim.x;
+    const int c0 = blockIdx.x;
+    const int warp = threadIdx.x >> 5;
     const unsigned lane = threadIdx.x & 31u;
-    float S[QN][NLEV];
+    if (threadIdx.x == 0) {
 #pragma unroll
-    for (int q = 0; q < QN; ++q) {
-        float F[NH];
-#pragma unroll
-        for (int h = 1; h <= NH; ++h) F[h - 1] = seg[base[h - 1] + ((256 * q * h) >> LOGNH)];
-        float s = F[NH - 1];
-        S[q][0] = s;
-#pragma unroll
-        for (int L = 1; L < NLEV; ++L) {
-            const int n = 1 << L;
-            const int step = NH / n;
-#pragma unroll
-            for (int h = 1; h <= n; h += 2) s += F[h * step - 1];
-            S[q][L] = s;
+        for (int s = 0; s < kHsStages; ++s) {
+            mbar_init(&full[s], 1);
+            mbar_init(&empty[s], kHsConsumerWarps);
         }
     }
-    if (s_out) {
+    __syncthreads();
+
+    if (warp == kHsConsumerWarps) {
+        // ---- producer warp: lane h - 1 copies segment h ----
+        const int h = (int)lane + 1;
+        const bool copier = h <= NH;
+        int soff = 0, slen = 0;
 #pragma unroll
-        for (int q = 0; q < QN; ++q) {
-            const int k = k0 + (int)threadIdx.x + 256 * q;
-#pragma unroll
-            for (int L = 0; L < NLEV; ++L)
-                s_out[((int64_t)tl * NLEV + L) * p.M + k] = (k >= 1) ? S[q][L] : 0.f;
+        for (int hh = 1; hh <= NH; ++hh)
+            if (hh == h) soff = Gm::off(hh), slen = Gm::len(hh);
+        int i = 0;
+        for (;; ++i) {
+            const int j = c0 + i * G;
+            if (j >= ntiles) break;
+            const int s = i % kHsStages;
+            if (i >= kHsStages &&
+                !mbar_wait_parity(&empty[s], (uint32_t)(((i / kHsStages) - 1) & 1))) {
+                if (lane == 0) atomicOr(count + 1, 1ull);
+                break;
+            }
+            const int tl = j >> logtpt;
+            const int k0 = (j & ((1 << logtpt) - 1)) << 10;
+            if (lane == 0) mbar_expect_tx(&full[s], Gm::BYTES);
+            __syncwarp();
+            if (copier)
+                tma_load_1d(seg + s * SEG + soff, Pw + ((int64_t)tl << p.logM) + ((k0 * h) >> LOGNH),
+                            (uint32_t)slen * 4u, &full[s]);
         }
+        // let the copies issued last land before the CTA's shared memory can go away
+        for (int m = (i > kHsStages ? i - kHsStages : 0); m < i; ++m)
+            (void)mbar_wait_parity(&full[m % kHsStages], (uint32_t)((m / kHsStages) & 1));
+        return;
     }
-    bool any = false;
+
+    // ---- consumer warps: thread t sums bins k0 + t + 256 q ----
+    const int t = (int)threadIdx.x;
+    uint32_t addr[NH];  // shared address of term h of bin k0 + t in stage 0
 #pragma unroll
-    for (int q = 0; q < QN; ++q)
+    for (int h = 1; h <= NH; ++h)
+        addr[h - 1] = smem_u32(seg) + 4u * (uint32_t)(Gm::off(h) + ((t * h + (NH >> 1)) >> LOGNH));
+    for (int i0 = 0;; i0 += kHsStages) {
 #pragma unroll
-        for (int L = 0; L < NLEV; ++L)
-            any |= (S[q][L] >= thr.v[L]) && (k0 + (int)threadIdx.x + 256 * q >= 1);
-    if (!__any_sync(0xffffffffu, any)) return;
+        for (int s = 0; s < kHsStages; ++s) {
+            const int i = i0 + s;
+            const int j = c0 + i * G;
+            if (j >= ntiles) return;
+            if (!mbar_wait_parity(&full[s], (uint32_t)((i / kHsStages) & 1))) {
+                if (lane == 0) atomicOr(count + 1, 1ull);
+                return;
+            }
+            float acc[QN];
+            float S[QN][NLEV];
 #pragma unroll
-    for (int q = 0; q < QN; ++q) {
-        const int k = k0 + (int)threadIdx.x + 256 * q;
-        const bool valid = k >= 1;
+            for (int L = 0; L < NLEV; ++L) {
+                const int step = NH >> L;
 #pragma unroll
-        for (int L = 0; L < NLEV; ++L) {
-            const bool hit = valid && (S[q][L] >= thr.v[L]);
-            const unsigned m = __ballot_sync(0xffffffffu, hit);
-            if (m) {
-                const int leader = __ffs(m) - 1;
-                unsigned long long b0 = 0;
-                if ((int)lane == leader) b0 = atomicAdd(count, (unsigned long long)__popc(m));
-                b0 = __shfl_sync(0xffffffffu, b0, leader);
-                if (hit) {
-                    const unsigned long long pos = b0 + __popc(m & ((1u << lane) - 1u));
-                    if ((int64_t)pos < cap) {
-                        Cand c;
-                        c.tidx = (uint32_t)(tidx0 + tl);
-                        c.nharm = (uint16_t)(1 << L);
-                        c.flags = 0;
-                        c.bin = (uint32_t)k;
-                        c.power = S[q][L];
-                        cands[pos] = c;
+                for (int h = step; h <= NH; h += 2 * step) {
+#pragma unroll
+                    for (int q = 0; q < QN; ++q) {
+                        float f;
+                        asm volatile("ld.shared.f32 %0, [%1];"
+                                     : "=f"(f)
+                                     : "r"(addr[h - 1] + 4u * (uint32_t)(s * SEG + ((CT * q * h) >> LOGNH))));
+                        acc[q] = (L == 0) ? f : acc[q] + f;
+                    }
+                }
+#pragma unroll
+                for (int q = 0; q < QN; ++q) S[q][L] = acc[q];
+            }
+            __syncwarp();
+            if (lane == 0) mbar_arrive(&empty[s]);  // stage s may be refilled
+            const int tl = j >> logtpt;
+            const int kk = ((j & ((1 << logtpt) - 1)) << 10) + t;
+            if (s_out) {
+#pragma unroll
+                for (int q = 0; q < QN; ++q) {
+                    const int k = kk + CT * q;
+#pragma unroll
+                    for (int L = 0; L < NLEV; ++L)
+                        s_out[((int64_t)tl * NLEV + L) * p.M + k] = (k >= 1) ? S[q][L] : 0.f;
+                }
+            }
+            bool any = false;
+#pragma unroll
+            for (int L = 0; L < NLEV; ++L) {
+                float m = S[0][L];
+#pragma unroll
+                for (int q = 1; q < QN; ++q) m = fmaxf(m, S[q][L]);
+                any |= m >= thr.v[L];
+            }
+            if (!__any_sync(0xffffffffu, any)) continue;
+#pragma unroll
+            for (int q = 0; q < QN; ++q) {
+                const int k = kk + CT * q;
+                const bool valid = k >= 1;
+#pragma unroll
+                for (int L = 0; L < NLEV; ++L) {
+                    const bool hit = valid && (S[q][L] >= thr.v[L]);
+                    const unsigned mk = __ballot_sync(0xffffffffu, hit);
+                    if (mk) {
+                        const int leader = __ffs(mk) - 1;
+                        unsigned long long b0 = 0;
+                        if ((int)lane == leader) b0 = atomicAdd(count, (unsigned long long)__popc(mk));
+                        b0 = __shfl_sync(0xffffffffu, b0, leader);
+                        if (hit) {
+                            const unsigned long long pos = b0 + __popc(mk & ((1u << lane) - 1u));
+                            if ((int64_t)pos < cap) {
+                                Cand cd;
+                                cd.tidx = (uint32_t)(tidx0 + tl);
+                                cd.nharm = (uint16_t)(1 << L);
+                                cd.flags = 0;
+                                cd.bin = (uint32_t)k;
+                                cd.power = S[q][L];
+                                cands[pos] = cd;
+                            }
+                        }
                     }
                 }
             }
@@ -469,21 +443,66 @@ cudaError_t launch_whitened(const float* P, const float* scale, int nt, const Pl
     return cudaGetLastError();
 }
 
+namespace {
+
+// Once per device and H: the stage ring's dynamic shared memory and the resident CTAs per
+// SM it allows (host-side attributes and queries only, so this is safe during capture).
+template <int NH>
+cudaError_t hs_shape(int& ctas)
+{
+    static std::mutex mu;
+    static int cached[64] = {};
+    int dev = 0;
+    cudaError_t e = cudaGetDevice(&dev);
+    if (e != cudaSuccess) return e;
+    if (dev < 0 || dev >= 64) return cudaErrorInvalidDevice;
+    std::lock_guard<std::mutex> lk(mu);
+    if (!cached[dev]) {
+        const int smem = (int)HsGeom<NH>::SMEM;
+        e = cudaFuncSetAttribute(k_harmsum<NH>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
+        if (e != cudaSuccess) return e;
+        int per_sm = 0, nsm = 0;
+        e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_harmsum<NH>, kHsThreads, smem);
+        if (e != cudaSuccess) return e;
+        e = cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev);
+        if (e != cudaSuccess) return e;
+        cached[dev] = std::max(1, per_sm) * std::max(1, nsm);
+    }
+    ctas = cached[dev];
+    return cudaSuccess;
+}
+
+template <int NH>
+cudaError_t launch_hs(const float* P, int nt, int64_t tidx0, const Plan& p, const Thr& thr,
+                      Cand* cands, int64_t cap, unsigned long long* count, float* s_out,
+                      cudaStream_t s)
+{
+    int ctas = 0;
+    cudaError_t e = hs_shape<NH>(ctas);
+    if (e != cudaSuccess) return e;
+    const int64_t ntiles = (p.M / kHsTile) * (int64_t)nt;
+    if (ntiles < 1 || ntiles > INT32_MAX) return cudaErrorInvalidValue;
+    const int grid = (int)std::min<int64_t>(ntiles, ctas);
+    k_harmsum<NH><<<grid, kHsThreads, HsGeom<NH>::SMEM, s>>>(P, p, tidx0, thr, cands, cap, count,
+                                                                  s_out, (int)ntiles);
+    return cudaGetLastError();
+}
+
+}  // namespace
+
 cudaError_t launch_harmsum(const float* P, const float* scale, int nt, int64_t tidx0,
                            const Plan& p, const Thr& thr, Cand* cands, int64_t cap,
                            unsigned long long* count, float* s_out, cudaStream_t s)
 {
     (void)scale;
-    dim3 grid((unsigned)(p.M / kHsTile), (unsigned)nt);
     switch (p.nharm) {
-        case 1: k_harmsum_tma<1><<<grid, 256, 0, s>>>(P, p, tidx0, thr, cands, cap, count, s_out); break;
-        case 2: k_harmsum_tma<2><<<grid, 256, 0, s>>>(P, p, tidx0, thr, cands, cap, count, s_out); break;
-        case 4: k_harmsum_tma<4><<<grid, 256, 0, s>>>(P, p, tidx0, thr, cands, cap, count, s_out); break;
-        case 8: k_harmsum_tma<8><<<grid, 256, 0, s>>>(P, p, tidx0, thr, cands, cap, count, s_out); break;
-        case 16: k_harmsum_tma<16><<<grid, 256, 0, s>>>(P, p, tidx0, thr, cands, cap, count, s_out); break;
+        case 1: return launch_hs<1>(P, nt, tidx0, p, thr, cands, cap, count, s_out, s);
+        case 2: return launch_hs<2>(P, nt, tidx0, p, thr, cands, cap, count, s_out, s);
+        case 4: return launch_hs<4>(P, nt, tidx0, p, thr, cands, cap, count, s_out, s);
+        case 8: return launch_hs<8>(P, nt, tidx0, p, thr, cands, cap, count, s_out, s);
+        case 16: return launch_hs<16>(P, nt, tidx0, p, thr, cands, cap, count, s_out, s);
         default: return cudaErrorInvalidValue;
     }
-    return cudaGetLastError();
 }
 
 }  // namespace bps
