@@ -132,11 +132,16 @@ __device__ __forceinline__ void fft_stage(float2* buf, int logL, int logNs, int 
     const int Q = 1 << logQ;
     const int Ns = 1 << logNs;
     const int twshift = 13 - logNs - LOGRADIX;  // 8192 / (Ns * RADIX)
+    const int nthr = (1 << (logL + lognl)) / EPT;  // == blockDim.x
+    // the butterflies of one thread (b = tid + i nthr) share k = j mod Ns, and so their
+    // twiddles, when nthr steps j by a multiple of Ns
+    const bool shared_k = LINE_FAST ? (((nthr >> lognl) & (Ns - 1)) == 0) : ((nthr & (Q - 1)) == 0);
     float2 v[EPT];
+    float2 w[RADIX];
     int dst[BPT], lskv[BPT];
 #pragma unroll
     for (int i = 0; i < BPT; ++i) {
-        const int b = threadIdx.x + i * blockDim.x;
+        const int b = threadIdx.x + i * nthr;
         int line, j;
         if (LINE_FAST) {
             line = b & ((1 << lognl) - 1);
@@ -154,12 +159,13 @@ __device__ __forceinline__ void fft_stage(float2* buf, int logL, int logNs, int 
         if (logNs > 0) {
             // twiddles W^{k s}, s = 1..RADIX-1, from one table load: W^{2^m} by squaring,
             // the others as products of two lower powers (at most 4 products deep)
-            float2 w[RADIX];
-            w[1] = __ldg(tw + (k << twshift));
+            if (i == 0 || !shared_k) {
+                w[1] = __ldg(tw + (k << twshift));
 #pragma unroll
-            for (int s = 2; s < RADIX; ++s) {
-                const int hb = (s & (s - 1)) == 0 ? (s >> 1) : (1 << (31 - __clz(s)));
-                w[s] = cmul(w[hb], w[s - hb]);
+                for (int s = 2; s < RADIX; ++s) {
+                    const int hb = (s & (s - 1)) == 0 ? (s >> 1) : (1 << (31 - __clz(s)));
+                    w[s] = cmul(w[hb], w[s - hb]);
+                }
             }
 #pragma unroll
             for (int s = 1; s < RADIX; ++s) v[i * RADIX + s] = cmul(v[i * RADIX + s], w[s]);
@@ -221,20 +227,21 @@ __device__ __forceinline__ float2 twiddle(uint32_t t, int logD)
 // (index map fast path for all of them, compensated branch for the rare
 // near-boundary ones), transforms them in registers and writes the 16 outputs.
 template <int LOGR_LAST>
-__device__ __forceinline__ void pass1_last_stage(const float2* __restrict__ sm, const Plan& p,
-                                                 int c0, int logNs, const float2* __restrict__ tw,
+__device__ __forceinline__ void pass1_last_stage(const float2* __restrict__ sm, int logG, int logC,
+                                                 int logM, int c0, int logNs,
+                                                 const float2* __restrict__ tw,
                                                  float2* __restrict__ Yt)
 {
     constexpr int RL = 1 << LOGR_LAST;
     constexpr int BPT = kEPT / RL;
-    const int logG = p.logG;
     const int G = 1 << logG;
     const int Ns = 1 << logNs;  // = R / RL: j < Ns, outputs at k1 = j + s Ns
     const int twshift = 13 - logNs - LOGR_LAST;
-    const uint32_t Mm = (uint32_t)(p.M - 1);
+    const uint32_t Mm = (uint32_t)((1 << logM) - 1);
+    const int nthr = (Ns * RL << logG) / kEPT;  // == blockDim.x
 #pragma unroll
     for (int i = 0; i < BPT; ++i) {
-        const int b = threadIdx.x + i * blockDim.x;
+        const int b = threadIdx.x + i * nthr;
         const int g = b & (G - 1);
         const int j = b >> logG;
         float2 v[RL];
@@ -255,10 +262,10 @@ __device__ __forceinline__ void pass1_last_stage(const float2* __restrict__ sm, 
         // four-step twiddle W_M^{j2 k1}, k1 = j + s Ns: W_M^{j2 j} (W_M^{j2 Ns})^s
         const uint32_t j2 = (uint32_t)(c0 + g);
         float2 u[RL];
-        u[0] = twiddle((j2 * (uint32_t)j) & Mm, p.logM);
+        u[0] = twiddle((j2 * (uint32_t)j) & Mm, logM);
         if (RL > 1) {
             float2 st[RL];
-            st[1] = twiddle((j2 * (uint32_t)Ns) & Mm, p.logM);
+            st[1] = twiddle((j2 * (uint32_t)Ns) & Mm, logM);
 #pragma unroll
             for (int s = 2; s < RL; ++s) {
                 const int hb = (s & (s - 1)) == 0 ? (s >> 1) : (1 << (31 - __clz(s)));
@@ -270,11 +277,14 @@ __device__ __forceinline__ void pass1_last_stage(const float2* __restrict__ sm, 
 #pragma unroll
         for (int s = 0; s < RL; ++s) {
             const int k1 = j + s * Ns;
-            Yt[((int64_t)k1 << p.logC) + j2] = cmul(v[Radix<LOGR_LAST>::out_pos(s)], u[s]);
+            Yt[((int64_t)k1 << logC) + j2] = cmul(v[Radix<LOGR_LAST>::out_pos(s)], u[s]);
         }
     }
 }
 
+// LR, LC, LG >= 0: log R, log C, log G fixed at compile time (index arithmetic folds
+// into constants); -1: taken from the plan.
+template <int LR, int LC, int LG>
 __global__ void __launch_bounds__(512, 1) k_pass1(SeriesView x, const Anchor* __restrict__ anc,
                                                   Plan p, const float2* __restrict__ tw,
                                                   float2* __restrict__ Y)
@@ -282,13 +292,15 @@ __global__ void __launch_bounds__(512, 1) k_pass1(SeriesView x, const Anchor* __
     extern __shared__ float2 sm[];
     resolve_fill(x);
     const int tl = blockIdx.y;
-    const int logG = p.logG;
+    const int logG = LG >= 0 ? LG : p.logG;
     const int G = 1 << logG;
-    const int logR = p.logR;
+    const int logR = LR >= 0 ? LR : p.logR;
+    const int logC = LC >= 0 ? LC : p.logC;
+    const int logM = (LR >= 0 && LC >= 0) ? LR + LC : p.logM;
     const int logQ = logR - 4;  // rows between the 16 elements of a first-stage butterfly
-    const int nthr = blockDim.x;
+    const int nthr = (1 << (logR + logG)) / kEPT;  // == blockDim.x
     const int c0 = blockIdx.x << logG;
-    const int n = (int)p.n;
+    const int n = 2 << logM;
     const int half = 1 << (p.logB - 1);
     const Anchor* at = anc + (int64_t)tl * p.nanchor;
     constexpr int BPT1 = kEPT / 16;
@@ -301,7 +313,7 @@ __global__ void __launch_bounds__(512, 1) k_pass1(SeriesView x, const Anchor* __
         unsigned pm = 0;
 #pragma unroll
         for (int s = 0; s < 16; ++s) {
-            const int m = 2 * (((j + (s << logQ)) << p.logC) + c0 + g);
+            const int m = 2 * (((j + (s << logQ)) << logC) + c0 + g);
             const int ab = m >> p.logB;
             const float4 a4 = __ldg(reinterpret_cast<const float4*>(at + ab));
             const float q3 = __ldg(&at[ab].q3);
@@ -323,7 +335,7 @@ __global__ void __launch_bounds__(512, 1) k_pass1(SeriesView x, const Anchor* __
             for (int q = 0; q < 32; ++q) {
                 if (pm & (1u << q)) {
                     const int s = q >> 1, u = q & 1;
-                    const int m = 2 * (((j + (s << logQ)) << p.logC) + c0 + g);
+                    const int m = 2 * (((j + (s << logQ)) << logC) + c0 + g);
                     const int ab = m >> p.logB;
                     const Anchor a = at[ab];
                     const int d = m - ((ab << p.logB) + half);
@@ -343,12 +355,12 @@ __global__ void __launch_bounds__(512, 1) k_pass1(SeriesView x, const Anchor* __
     int logNs = 4;
     for (; logNs + 4 < logR; logNs += 4)
         fft_stage<4, kEPT, true>(sm, logR, logNs, logG, 1, G, 0, tw);
-    float2* Yt = Y + (int64_t)tl * p.M;
+    float2* Yt = Y + ((int64_t)tl << logM);
     switch (logR - logNs) {
-        case 4: pass1_last_stage<4>(sm, p, c0, logNs, tw, Yt); break;
-        case 3: pass1_last_stage<3>(sm, p, c0, logNs, tw, Yt); break;
-        case 2: pass1_last_stage<2>(sm, p, c0, logNs, tw, Yt); break;
-        default: pass1_last_stage<1>(sm, p, c0, logNs, tw, Yt); break;
+        case 4: pass1_last_stage<4>(sm, logG, logC, logM, c0, logNs, tw, Yt); break;
+        case 3: pass1_last_stage<3>(sm, logG, logC, logM, c0, logNs, tw, Yt); break;
+        case 2: pass1_last_stage<2>(sm, logG, logC, logM, c0, logNs, tw, Yt); break;
+        default: pass1_last_stage<1>(sm, logG, logC, logM, c0, logNs, tw, Yt); break;
     }
 }
 
@@ -369,19 +381,25 @@ __device__ __forceinline__ void power_pair(float2 zk, float2 zm, float2 w, float
 // Pass 2: C-point FFTs of NP row pairs (q, R - q), q in [q0, q0 + NP) (pair 0 holds
 // the self-mirrored rows 0 and R/2), then real-FFT split and power.  Items are
 // assigned q-fastest so each warp writes NP consecutive bins per k2.
+// LR, LC, LNP >= 0: log R, log C, log NP fixed at compile time; -1: from the plan.
+template <int LR, int LC, int LNP>
 __global__ void __launch_bounds__(512, 1) k_pass2(const float2* __restrict__ Y, Plan p,
                                                   const float2* __restrict__ tw,
                                                   float* __restrict__ P)
 {
     extern __shared__ float2 sm[];
     const int tl = blockIdx.y;
-    const int logR = p.logR, logC = p.logC;
+    const int logR = LR >= 0 ? LR : p.logR;
+    const int logC = LC >= 0 ? LC : p.logC;
+    const int logM = logR + logC;
+    const int logn = logM + 1;
+    const int64_t M = (int64_t)1 << logM;
     const int R = 1 << logR, C = 1 << logC;
-    const int logNP = p.logNP;
+    const int logNP = LNP >= 0 ? LNP : p.logNP;
     const int NP = 1 << logNP;
     const int q0 = blockIdx.x << logNP;
-    const int nthr = blockDim.x;
-    const float2* Yt = Y + (int64_t)tl * p.M;
+    const int nthr = (NP * C * 2) / kEPT;  // == blockDim.x
+    const float2* Yt = Y + (int64_t)tl * M;
     // lines [0, NP): low rows q0 + l ; lines [NP, 2NP): their mirrors.  Line l starts
     // at pad(l*C) + l*skew: the skew spreads the NP lines a warp reads in the split
     // phase over distinct banks.  The first radix-16 stage (Ns = 1) is fused with the
@@ -389,7 +407,7 @@ __global__ void __launch_bounds__(512, 1) k_pass2(const float2* __restrict__ Y, 
     const int skew = 32 >> logNP;
     const int logQ = logC - 4;
     constexpr int BPT1 = kEPT / 16;
-#pragma unroll 1
+#pragma unroll
     for (int i = 0; i < BPT1; ++i) {
         const int b = threadIdx.x + i * nthr;
         const int j = b & ((1 << logQ) - 1);
@@ -416,11 +434,11 @@ __global__ void __launch_bounds__(512, 1) k_pass2(const float2* __restrict__ Y, 
         else if (rem == 2) fft_stage<2, kEPT, false>(sm, logC, logNs, logNP + 1, C, 1, skew, tw);
         else if (rem == 1) fft_stage<1, kEPT, false>(sm, logC, logNs, logNP + 1, C, 1, skew, tw);
     }
-    float* Pt = P + (int64_t)tl * p.M;
+    float* Pt = P + (int64_t)tl * M;
     // W_N^{q + R k2} = W_N^q * W_{2C}^{k2};  W_{2C}^{k2} = tw[k2 * 8192 / (2C)]
     const int ql = threadIdx.x & (NP - 1);
     const int q = q0 + ql;
-    const float2 wq = twiddle((uint32_t)q, p.logn);
+    const float2 wq = twiddle((uint32_t)q, logn);
     const int twsh = 12 - logC;
     const int lowl = ql, highl = NP + ql;
     const int lo0 = lowl * skew, hi0 = highl * skew;
@@ -434,7 +452,7 @@ __global__ void __launch_bounds__(512, 1) k_pass2(const float2* __restrict__ Y, 
             power_pair(sm[pad(lowl * C + k2) + lo0], sm[pad(highl * C + (C - 1 - k2)) + hi0], w,
                        pa, pb);
             Pt[k] = pa;
-            Pt[p.M - k] = pb;
+            Pt[M - k] = pb;
         } else {
             if (k2 <= (C >> 1)) {  // row 0: bins R k2 and M - R k2
                 const int64_t k = (int64_t)k2 << logR;
@@ -445,18 +463,18 @@ __global__ void __launch_bounds__(512, 1) k_pass2(const float2* __restrict__ Y, 
                     Pt[0] = 0.f;
                 } else {
                     Pt[k] = pa;
-                    if (k2 != (C >> 1)) Pt[p.M - k] = pb;
+                    if (k2 != (C >> 1)) Pt[M - k] = pb;
                 }
             }
             if (k2 < (C >> 1)) {  // row R/2: bins R/2 + R k2 and M - (R/2 + R k2)
                 const int64_t k = (R >> 1) + ((int64_t)k2 << logR);
                 const float2 w =
-                    cmul(twiddle((uint32_t)(R >> 1), p.logn), __ldg(tw + (k2 << twsh)));
+                    cmul(twiddle((uint32_t)(R >> 1), logn), __ldg(tw + (k2 << twsh)));
                 float pa, pb;
                 power_pair(sm[pad(highl * C + k2) + hi0], sm[pad(highl * C + (C - 1 - k2)) + hi0],
                            w, pa, pb);
                 Pt[k] = pa;
-                Pt[p.M - k] = pb;
+                Pt[M - k] = pb;
             }
         }
     }
@@ -475,6 +493,36 @@ __global__ void k_power_r2c(const float2* __restrict__ X, Plan p, float* __restr
 // padded tile plus the pass-2 line skew (at most 32 complex in total)
 size_t tile_smem(int logt) { return (size_t)(((1 << logt) + ((1 << logt) >> 4) + 64) * sizeof(float2)); }
 
+// Compile-time geometries of the two passes for 2^21..2^25 samples at pass-1 tiles 2^13 /
+// 2^14 and pass-2 tiles 2^13 / 2^14 (other plans use the <-1, -1, -1> kernels).
+using Pass1Fn = void (*)(SeriesView, const Anchor*, Plan, const float2*, float2*);
+using Pass2Fn = void (*)(const float2*, Plan, const float2*, float*);
+
+#define BPS_PASS1_GEOMETRIES(X) \
+    X(10, 10, 4) X(10, 10, 3) X(11, 10, 3) X(11, 10, 2) X(12, 10, 2) X(12, 10, 1) X(13, 10, 1) \
+    X(13, 10, 0) X(13, 11, 1) X(13, 11, 0) X(-1, -1, -1)
+#define BPS_PASS2_GEOMETRIES(X) \
+    X(10, 10, 2) X(10, 10, 3) X(11, 10, 2) X(11, 10, 3) X(12, 10, 2) X(12, 10, 3) X(13, 10, 2) \
+    X(13, 10, 3) X(13, 11, 1) X(13, 11, 2) X(-1, -1, -1)
+
+Pass1Fn pick_pass1(const Plan& p)
+{
+#define BPS_PICK(a, b, c) \
+    if ((a < 0) || (p.logR == a && p.logC == b && p.logG == c)) return k_pass1<a, b, c>;
+    BPS_PASS1_GEOMETRIES(BPS_PICK)
+#undef BPS_PICK
+    return k_pass1<-1, -1, -1>;
+}
+
+Pass2Fn pick_pass2(const Plan& p)
+{
+#define BPS_PICK(a, b, c) \
+    if ((a < 0) || (p.logR == a && p.logC == b && p.logNP == c)) return k_pass2<a, b, c>;
+    BPS_PASS2_GEOMETRIES(BPS_PICK)
+#undef BPS_PICK
+    return k_pass2<-1, -1, -1>;
+}
+
 }  // namespace
 
 // Large dynamic shared memory for the FFT passes, set once per device (a host-side
@@ -488,9 +536,17 @@ cudaError_t set_smem_attributes()
     if (e != cudaSuccess || dev < 0 || dev >= 64) return e != cudaSuccess ? e : cudaErrorInvalidDevice;
     std::lock_guard<std::mutex> lk(mu);
     if (done[dev]) return cudaSuccess;
-    e = cudaFuncSetAttribute(k_pass1, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)tile_smem(kLogTile));
-    if (e == cudaSuccess)
-        e = cudaFuncSetAttribute(k_pass2, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)tile_smem(kLogTile));
+    const int bytes = (int)tile_smem(kLogTile);
+#define BPS_ATTR(a, b, c) \
+    if (e == cudaSuccess)  \
+        e = cudaFuncSetAttribute(k_pass1<a, b, c>, cudaFuncAttributeMaxDynamicSharedMemorySize, bytes);
+    BPS_PASS1_GEOMETRIES(BPS_ATTR)
+#undef BPS_ATTR
+#define BPS_ATTR(a, b, c) \
+    if (e == cudaSuccess)  \
+        e = cudaFuncSetAttribute(k_pass2<a, b, c>, cudaFuncAttributeMaxDynamicSharedMemorySize, bytes);
+    BPS_PASS2_GEOMETRIES(BPS_ATTR)
+#undef BPS_ATTR
     if (e == cudaSuccess) done[dev] = true;
     return e;
 }
@@ -508,7 +564,7 @@ cudaError_t launch_pass1(const SeriesView& x, const Anchor* anc, int nt, const P
     cudaError_t e = set_smem_attributes();
     if (e != cudaSuccess) return e;
     dim3 grid((unsigned)(1 << (p.logC - p.logG)), (unsigned)nt);
-    k_pass1<<<grid, (1 << logt) / kEPT, tile_smem(logt), s>>>(x, anc, p, tw, Y);
+    pick_pass1(p)<<<grid, (1 << logt) / kEPT, tile_smem(logt), s>>>(x, anc, p, tw, Y);
     return cudaGetLastError();
 }
 
@@ -519,7 +575,7 @@ cudaError_t launch_pass2(const float2* Y, int nt, const Plan& p, const float2* t
     cudaError_t e = set_smem_attributes();
     if (e != cudaSuccess) return e;
     dim3 grid((unsigned)(1 << (p.logR - 1 - p.logNP)), (unsigned)nt);
-    k_pass2<<<grid, (1 << logt) / kEPT, tile_smem(logt), s>>>(Y, p, tw, P);
+    pick_pass2(p)<<<grid, (1 << logt) / kEPT, tile_smem(logt), s>>>(Y, p, tw, P);
     return cudaGetLastError();
 }
 
