@@ -239,6 +239,19 @@ __device__ __forceinline__ void pass1_last_stage(const float2* __restrict__ sm, 
     const int twshift = 13 - logNs - LOGR_LAST;
     const uint32_t Mm = (uint32_t)((1 << logM) - 1);
     const int nthr = (Ns * RL << logG) / kEPT;  // == blockDim.x
+    // four-step twiddle W_M^{j2 k1}, k1 = j + s Ns: W_M^{j2 j} (W_M^{j2 Ns})^s.  The
+    // column j2 = c0 + (tid mod G) is the same for all of a thread's butterflies (nthr is
+    // a multiple of G), so the powers st[s] = (W_M^{j2 Ns})^s are computed once.
+    const uint32_t j2 = (uint32_t)(c0 + (threadIdx.x & (G - 1)));
+    float2 st[RL];
+    if (RL > 1) {
+        st[1] = twiddle((j2 * (uint32_t)Ns) & Mm, logM);
+#pragma unroll
+        for (int s = 2; s < RL; ++s) {
+            const int hb = (s & (s - 1)) == 0 ? (s >> 1) : (1 << (31 - __clz(s)));
+            st[s] = cmul(st[hb], st[s - hb]);
+        }
+    }
 #pragma unroll
     for (int i = 0; i < BPT; ++i) {
         const int b = threadIdx.x + i * nthr;
@@ -259,21 +272,10 @@ __device__ __forceinline__ void pass1_last_stage(const float2* __restrict__ sm, 
             for (int s = 1; s < RL; ++s) v[s] = cmul(v[s], w[s]);
         }
         Radix<LOGR_LAST>::dft(v);
-        // four-step twiddle W_M^{j2 k1}, k1 = j + s Ns: W_M^{j2 j} (W_M^{j2 Ns})^s
-        const uint32_t j2 = (uint32_t)(c0 + g);
         float2 u[RL];
         u[0] = twiddle((j2 * (uint32_t)j) & Mm, logM);
-        if (RL > 1) {
-            float2 st[RL];
-            st[1] = twiddle((j2 * (uint32_t)Ns) & Mm, logM);
 #pragma unroll
-            for (int s = 2; s < RL; ++s) {
-                const int hb = (s & (s - 1)) == 0 ? (s >> 1) : (1 << (31 - __clz(s)));
-                st[s] = cmul(st[hb], st[s - hb]);
-            }
-#pragma unroll
-            for (int s = 1; s < RL; ++s) u[s] = cmul(u[0], st[s]);
-        }
+        for (int s = 1; s < RL; ++s) u[s] = cmul(u[0], st[s]);
 #pragma unroll
         for (int s = 0; s < RL; ++s) {
             const int k1 = j + s * Ns;
@@ -401,10 +403,12 @@ __global__ void __launch_bounds__(512, 1) k_pass2(const float2* __restrict__ Y, 
     const int nthr = (NP * C * 2) / kEPT;  // == blockDim.x
     const float2* Yt = Y + (int64_t)tl * M;
     // lines [0, NP): low rows q0 + l ; lines [NP, 2NP): their mirrors.  Line l starts
-    // at pad(l*C) + l*skew: the skew spreads the NP lines a warp reads in the split
-    // phase over distinct banks.  The first radix-16 stage (Ns = 1) is fused with the
-    // load: butterfly (line, j) reads elements j + s C/16 of its row straight from Y.
-    const int skew = 32 >> logNP;
+    // at pad(l*C) + l*skew (pad(l*C) is a multiple of 16 complex).  In the split phase a
+    // half-warp reads NP lines at 16/NP consecutive k2 each; skew = 16/NP puts the lines
+    // 16/NP complex apart modulo 16, i.e. on disjoint bank pairs (at most 64 complex of
+    // slack in all).  The first radix-16 stage (Ns = 1) is fused with the load:
+    // butterfly (line, j) reads elements j + s C/16 of its row straight from Y.
+    const int skew = logNP <= 4 ? (16 >> logNP) : (logNP == 5 ? 1 : 0);
     const int logQ = logC - 4;
     constexpr int BPT1 = kEPT / 16;
 #pragma unroll
