@@ -284,6 +284,49 @@ __device__ __forceinline__ void pass1_last_stage(const float2* __restrict__ sm, 
     }
 }
 
+// Source indices of the 32 samples of first-stage butterfly j of column col: complex
+// rows j + s R/16 (s < 16), real samples 2 (row C + col) + u (u < 2).  FP32 fast path of
+// the index map for all of them, the compensated branch for the rare ones whose
+// fractional part lies within the guard of a rounding boundary.
+__device__ __forceinline__ void pass1_indices(const Anchor* __restrict__ at, int logB, int logQ,
+                                              int logC, int col, int j, int (&id)[32])
+{
+    const int half = 1 << (logB - 1);
+    unsigned pm = 0;
+#pragma unroll
+    for (int s = 0; s < 16; ++s) {
+        const int m = 2 * (((j + (s << logQ)) << logC) + col);
+        const int ab = m >> logB;
+        const float4 a4 = __ldg(reinterpret_cast<const float4*>(at + ab));
+        const float q3 = __ldg(&at[ab].q3);
+        const int I = __float_as_int(a4.x);
+        const float fh = a4.y + 0.5f, L = a4.z, q2 = a4.w;
+        const int d = m - ((ab << logB) + half);
+#pragma unroll
+        for (int u = 0; u < 2; ++u) {
+            const float df = (float)(d + u);
+            const float xx = fh - df * fmaf(df, fmaf(df, q3, q2), L);
+            const float fl = floorf(xx);
+            const float fr = xx - fl;
+            if (!(fr > kGuard && fr < 1.f - kGuard)) pm |= 1u << (2 * s + u);
+            id[2 * s + u] = m + u + I + (int)fl;
+        }
+    }
+    if (pm) {
+#pragma unroll
+        for (int q = 0; q < 32; ++q) {
+            if (pm & (1u << q)) {
+                const int s = q >> 1, u = q & 1;
+                const int m = 2 * (((j + (s << logQ)) << logC) + col);
+                const int ab = m >> logB;
+                const Anchor a = at[ab];
+                const int d = m - ((ab << logB) + half);
+                id[q] = m + u + a.I + off_round_precise(a, d + u);
+            }
+        }
+    }
+}
+
 // LR, LC, LG >= 0: log R, log C, log G fixed at compile time (index arithmetic folds
 // into constants); -1: taken from the plan.
 template <int LR, int LC, int LG>
@@ -303,7 +346,6 @@ __global__ void __launch_bounds__(512, 1) k_pass1(SeriesView x, const Anchor* __
     const int nthr = (1 << (logR + logG)) / kEPT;  // == blockDim.x
     const int c0 = blockIdx.x << logG;
     const int n = 2 << logM;
-    const int half = 1 << (p.logB - 1);
     const Anchor* at = anc + (int64_t)tl * p.nanchor;
     constexpr int BPT1 = kEPT / 16;
 #pragma unroll 1
@@ -312,39 +354,7 @@ __global__ void __launch_bounds__(512, 1) k_pass1(SeriesView x, const Anchor* __
         const int g = b & (G - 1);
         const int j = b >> logG;
         int id[32];
-        unsigned pm = 0;
-#pragma unroll
-        for (int s = 0; s < 16; ++s) {
-            const int m = 2 * (((j + (s << logQ)) << logC) + c0 + g);
-            const int ab = m >> p.logB;
-            const float4 a4 = __ldg(reinterpret_cast<const float4*>(at + ab));
-            const float q3 = __ldg(&at[ab].q3);
-            const int I = __float_as_int(a4.x);
-            const float fh = a4.y + 0.5f, L = a4.z, q2 = a4.w;
-            const int d = m - ((ab << p.logB) + half);
-#pragma unroll
-            for (int u = 0; u < 2; ++u) {
-                const float df = (float)(d + u);
-                const float xx = fh - df * fmaf(df, fmaf(df, q3, q2), L);
-                const float fl = floorf(xx);
-                const float fr = xx - fl;
-                if (!(fr > kGuard && fr < 1.f - kGuard)) pm |= 1u << (2 * s + u);
-                id[2 * s + u] = m + u + I + (int)fl;
-            }
-        }
-        if (pm) {
-#pragma unroll
-            for (int q = 0; q < 32; ++q) {
-                if (pm & (1u << q)) {
-                    const int s = q >> 1, u = q & 1;
-                    const int m = 2 * (((j + (s << logQ)) << logC) + c0 + g);
-                    const int ab = m >> p.logB;
-                    const Anchor a = at[ab];
-                    const int d = m - ((ab << p.logB) + half);
-                    id[q] = m + u + a.I + off_round_precise(a, d + u);
-                }
-            }
-        }
+        pass1_indices(at, p.logB, logQ, logC, c0 + g, j, id);
         float2 v[16];
 #pragma unroll
         for (int s = 0; s < 16; ++s)

@@ -291,3 +291,27 @@ def test_autotune_choice_and_invariance(bps, ctx, w1):
     assert ms > 0
     got, _ = ctx.fetch_candidates(ctx.search(sid, bid, bps.default_params()))  # uses the choice
     assert np.array_equal(got, ref)
+
+
+@pytest.mark.parametrize("logn", [16, 19, 21])
+def test_pass1_tiles_identical(bps, ctx, logn):
+    """Pass-1 tiles of 2^13 and 2^14 complex (G = 2^13/R and 2^14/R columns per CTA,
+    different kernel instantiations) compute the same floats: every column FFT runs the
+    same operations in the same order whatever the tile."""
+    n, ts = 1 << logn, 64e-6
+    T = n * ts
+    p = synth.Pulsar(period_s=0.021, porb_s=5 * T, tau_lts=0.08, phi_rad=0.4, amp=0.3)
+    x = synth.inject(synth.noise(n, 1000 + logn), ts, p)
+    bank, _ = synth.uniform_bank(6, 2000 + logn, (3 * T, 10 * T), (0.0, 0.1),
+                                 true_orbits=[p.orbit()])
+    sid = ctx.load_series(x, ts)
+    bid = ctx.load_bank(bank)
+    res = {}
+    for lt in (13, 14):
+        prm = bps.default_params(log_tile=lt, log_tile2=13, sigma_thr=5.0)
+        res[lt] = (ctx.whitened_spectrum(sid, bid, 0, 6, n, prm),
+                   ctx.fetch_candidates(ctx.search(sid, bid, prm))[0])
+    assert np.array_equal(res[13][0], res[14][0])
+    assert np.array_equal(res[13][1], res[14][1]) and res[13][1].size > 0
+    ctx.unload(sid)
+    ctx.unload(bid)
