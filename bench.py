@@ -37,7 +37,7 @@ UNIT = "templates/s"
 #   pass1: series read 4N + packed-complex write 4N; pass2: 4N read + 2N power write;
 #   median: 2N read; harmsum: 2N read.  Whole path (one series read, whitened
 #   spectrum written once and read once): 8N.
-STAGE_BYTES_PER_N = {"pass1": 8.0, "pass2": 6.0, "median": 2.0, "harmsum": 2.0,
+STAGE_BYTES_PER_N = {"pass1": 8.0, "pass2": 6.0, "median": 4.0, "harmsum": 2.0,
                      "power": 4.0 + 2.0, "anchors": 0.0}
 PATH_BYTES_PER_N = 8.0
 CAND_CAP = 1 << 22
@@ -84,16 +84,18 @@ def kernel_source_hash():
     return h.hexdigest()[:16]
 
 
-def ncu_traffic(stage, workload):
-    """DRAM bytes per launch of `stage` from the committed ncu summary, or None when
-    absent or taken on different kernel sources."""
+def ncu_traffic(stage, workload, templates_per_launch):
+    """DRAM bytes per launch of `stage` from the committed ncu summary, scaled from the
+    captured launch's templates to this run's (the traffic of these kernels grows in
+    proportion to the templates a launch processes), or None when absent or taken on
+    different kernel sources."""
     try:
         with open(os.path.join(ROOT, "profiles", "traffic.json")) as f:
             d = json.load(f)
         e = d[workload][stage]
         if e.get("source_hash") != kernel_source_hash():
             return None
-        return float(e["dram_bytes_per_launch"])
+        return float(e["dram_bytes_per_launch"]) * templates_per_launch / float(e["templates_per_launch"])
     except Exception:
         return None
 
@@ -412,7 +414,7 @@ def main():
     per_launch_ms = stage_ms[dom] / max(1, stage_launch[dom])
     alg_bytes = STAGE_BYTES_PER_N[dom] * n * batch
     achieved = alg_bytes / (per_launch_ms * 1e-3) / 1e9
-    traffic = ncu_traffic(dom, "htru_2p%d" % args.logn)
+    traffic = ncu_traffic(dom, "htru_2p%d" % args.logn, batch)
     roof = {"bound": "hbm", "kernel": dom, "achieved": achieved, "peak": peak, "unit": "GB/s",
             "frac": achieved / peak, "peak_kind": peak_kind, "traffic": traffic,
             "alg_bytes_per_launch": alg_bytes, "templates_per_launch": batch,
