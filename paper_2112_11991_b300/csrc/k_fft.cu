@@ -26,7 +26,9 @@ namespace bps {
 
 namespace {
 
-constexpr int kEPT = 32;
+constexpr int kEPT = 32;   // elements per thread in pass 1 (two radix-16 butterflies)
+constexpr int kEPT2 = 16;  // elements per thread in pass 2 (one radix-16 butterfly; 64 registers,
+                           // twice the resident warps of 32)
 constexpr int kLogTile = 14;  // largest tile (complex values per CTA) of both passes
 
 __device__ __forceinline__ int pad(int i) { return i + (i >> 4); }
@@ -395,7 +397,7 @@ __device__ __forceinline__ void power_pair(float2 zk, float2 zm, float2 w, float
 // assigned q-fastest so each warp writes NP consecutive bins per k2.
 // LR, LC, LNP >= 0: log R, log C, log NP fixed at compile time; -1: from the plan.
 template <int LR, int LC, int LNP>
-__global__ void __launch_bounds__(512, 1) k_pass2(const float2* __restrict__ Y, Plan p,
+__global__ void __launch_bounds__(1024, 1) k_pass2(const float2* __restrict__ Y, Plan p,
                                                   const float2* __restrict__ tw,
                                                   float* __restrict__ P)
 {
@@ -410,7 +412,7 @@ __global__ void __launch_bounds__(512, 1) k_pass2(const float2* __restrict__ Y, 
     const int logNP = LNP >= 0 ? LNP : p.logNP;
     const int NP = 1 << logNP;
     const int q0 = blockIdx.x << logNP;
-    const int nthr = (NP * C * 2) / kEPT;  // == blockDim.x
+    const int nthr = (NP * C * 2) / kEPT2;  // == blockDim.x
     const float2* Yt = Y + (int64_t)tl * M;
     // lines [0, NP): low rows q0 + l ; lines [NP, 2NP): their mirrors.  Line l starts
     // at pad(l*C) + l*skew (pad(l*C) is a multiple of 16 complex).  In the split phase a
@@ -420,7 +422,7 @@ __global__ void __launch_bounds__(512, 1) k_pass2(const float2* __restrict__ Y, 
     // butterfly (line, j) reads elements j + s C/16 of its row straight from Y.
     const int skew = logNP <= 4 ? (16 >> logNP) : (logNP == 5 ? 1 : 0);
     const int logQ = logC - 4;
-    constexpr int BPT1 = kEPT / 16;
+    constexpr int BPT1 = kEPT2 / 16;
 #pragma unroll
     for (int i = 0; i < BPT1; ++i) {
         const int b = threadIdx.x + i * nthr;
@@ -442,11 +444,11 @@ __global__ void __launch_bounds__(512, 1) k_pass2(const float2* __restrict__ Y, 
     {
         int logNs = 4;
         for (; logNs + 4 <= logC; logNs += 4)
-            fft_stage<4, kEPT, false>(sm, logC, logNs, logNP + 1, C, 1, skew, tw);
+            fft_stage<4, kEPT2, false>(sm, logC, logNs, logNP + 1, C, 1, skew, tw);
         const int rem = logC - logNs;
-        if (rem == 3) fft_stage<3, kEPT, false>(sm, logC, logNs, logNP + 1, C, 1, skew, tw);
-        else if (rem == 2) fft_stage<2, kEPT, false>(sm, logC, logNs, logNP + 1, C, 1, skew, tw);
-        else if (rem == 1) fft_stage<1, kEPT, false>(sm, logC, logNs, logNP + 1, C, 1, skew, tw);
+        if (rem == 3) fft_stage<3, kEPT2, false>(sm, logC, logNs, logNP + 1, C, 1, skew, tw);
+        else if (rem == 2) fft_stage<2, kEPT2, false>(sm, logC, logNs, logNP + 1, C, 1, skew, tw);
+        else if (rem == 1) fft_stage<1, kEPT2, false>(sm, logC, logNs, logNP + 1, C, 1, skew, tw);
     }
     float* Pt = P + (int64_t)tl * M;
     // W_N^{q + R k2} = W_N^q * W_{2C}^{k2};  W_{2C}^{k2} = tw[k2 * 8192 / (2C)]
@@ -589,7 +591,7 @@ cudaError_t launch_pass2(const float2* Y, int nt, const Plan& p, const float2* t
     cudaError_t e = set_smem_attributes();
     if (e != cudaSuccess) return e;
     dim3 grid((unsigned)(1 << (p.logR - 1 - p.logNP)), (unsigned)nt);
-    pick_pass2(p)<<<grid, (1 << logt) / kEPT, tile_smem(logt), s>>>(Y, p, tw, P);
+    pick_pass2(p)<<<grid, (1 << logt) / kEPT2, tile_smem(logt), s>>>(Y, p, tw, P);
     return cudaGetLastError();
 }
 
