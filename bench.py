@@ -59,8 +59,14 @@ def parse():
                          "scale per 4096 samples (FFT arithmetic is FP32 either way)")
     ap.add_argument("--no-plain", action="store_true")
     ap.add_argument("--no-serving", action="store_true")
-    ap.add_argument("--serve-rate", type=float, default=20.0)
-    ap.add_argument("--serve-requests", type=int, default=32)
+    ap.add_argument("--serve-rates", default="1,5,20,50",
+                    help="Poisson request rates (req/s) of the serving sweep")
+    ap.add_argument("--serve-seconds", type=float, default=4.0,
+                    help="arrival window per rate (requests = max(8, rate x seconds))")
+    ap.add_argument("--no-uneven", action="store_true",
+                    help="skip the batched uneven-length workload (CUDA graph)")
+    ap.add_argument("--no-elliptical", action="store_true",
+                    help="skip the 2^25-sample elliptical FP16 workload")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--cpu-templates", type=int, default=0)
     ap.add_argument("--cpu-threads", type=int, default=0)
@@ -232,21 +238,28 @@ def run_reference(args, ws, rank):
     print(json.dumps(out), flush=True)
 
 
-def run_serving(bps, ctx, rate, nreq, seed=5):
+def serving_pool(seed=5):
+    """Seeded series for the serving sweep: three per length 2^20..2^24 at 64 us."""
+    return {logn: [synth.noise(1 << logn, 3000 + 10 * logn + i) for i in range(3)]
+            for logn in range(20, 25)}
+
+
+def run_serving(bps, ctx, rate, nreq, pool, seed=5):
     """Poisson stream of search requests into the continuously batched server: series
-    2^20..2^22 samples (log-uniform) at 64 us stored FP16, banks of 64..512 circular or
-    elliptical (e <= 0.1) templates.  Returns throughput and p50/p99 latency."""
+    2^20..2^24 samples (log-uniform) at 64 us stored FP16, banks of 64..4096 (log-uniform)
+    circular or elliptical (e <= 0.1) templates.  Returns throughput and p50/p99 latency
+    (submission to candidates on the host)."""
     import threading
-    rng = np.random.default_rng(seed)
+    rng = np.random.default_rng(seed + int(rate * 1000))
     reqs = []
     for i in range(nreq):
-        logn = int(rng.integers(20, 23))
-        n, ts = 1 << logn, 64e-6
-        T = n * ts
-        K = int(2 ** rng.uniform(6, 9))
+        logn = int(rng.integers(20, 25))
+        ts = 64e-6
+        T = (1 << logn) * ts
+        K = int(2 ** rng.uniform(6, 12))
         ecc = (0.0, 0.1) if rng.random() < 0.5 else None
         bank, _ = synth.uniform_bank(K, 1000 + i, (3 * T, 10 * T), (0.0, 0.5), ecc=ecc)
-        reqs.append((synth.noise(n, 2000 + i), ts, bank))
+        reqs.append((pool[logn][i % 3], ts, bank))
     gaps = rng.exponential(1.0 / rate, nreq)
     prm = bps.default_params(cand_cap=1 << 16)
     lat, tickets = [], []
@@ -278,10 +291,105 @@ def run_serving(bps, ctx, rate, nreq, seed=5):
     return {"rate_req_s": rate, "requests": nreq, "templates": templates,
             "templates_per_s": templates / wall, "wall_s": wall,
             "p50_ms": 1e3 * float(np.percentile(lat, 50)),
-            "p99_ms": 1e3 * float(np.percentile(lat, 99)),
-            "workload": "Poisson arrivals; series 2^20-2^22 x 64 us FP16 storage; banks 64-512 "
-                        "circular/elliptical templates; server max_active 4, 2 launch groups "
-                        "in flight per request"}
+            "p99_ms": 1e3 * float(np.percentile(lat, 99))}
+
+
+SERVING_WORKLOAD = ("Poisson arrivals; series 2^20-2^24 (log-uniform) x 64 us, FP16 storage; "
+                    "banks 64-4096 (log-uniform) circular or elliptical (e <= 0.1) templates; "
+                    "server max_active 4, 2 launch groups in flight per request, HBM budget "
+                    "0.9 x free; latency from submission to candidates on the host")
+
+
+def run_uneven(bps, ctx, steps=2, warmup=1, seed=11):
+    """Batched uneven search: 64 series of random length 2^21..2^24 at 64 us, each with
+    its own bank of 256..2048 circular templates (Porb U[3T,10T], tau U[0,3] lt-s, phi
+    U), launch shapes autotuned per length, all 64 searches captured in one CUDA graph and
+    replayed; device time per replay by CUDA events on the launching stream."""
+    import torch
+    rng = np.random.default_rng(seed)
+    pairs, K, n_of = [], 0, {}
+    ids = []
+    for i in range(64):
+        logn = int(rng.integers(21, 25))
+        n, ts = 1 << logn, 64e-6
+        T = n * ts
+        k = int(rng.integers(256, 2049))
+        bank, _ = synth.uniform_bank(k, 5000 + i, (3 * T, 10 * T), (0.0, 3.0))
+        sid = ctx.load_series(synth.noise(n, 6000 + i), ts)
+        bid = ctx.load_bank(bank)
+        ids += [sid, bid]
+        pairs.append((sid, bid))
+        n_of[logn] = (sid, bid)
+        K += k
+    prm = bps.default_params(cand_cap=1 << 20)
+    tuned = {}
+    for logn, (sid, bid) in sorted(n_of.items()):
+        best, _ = ctx.autotune(sid, bid, prm, sample_templates=64)
+        tuned[logn] = [best.log_tile, best.log_tile2, best.batch]
+    gid = ctx.graph_create(pairs, prm)
+    st = torch.cuda.Stream()
+    ms = []
+    for i in range(warmup + steps):
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        st.synchronize()
+        e0.record(st)
+        ctx.graph_launch(gid, st)
+        e1.record(st)
+        st.synchronize()
+        if i >= warmup:
+            ms.append(e0.elapsed_time(e1))
+    ncand = sum(ctx.graph_fetch(gid, j, allow_overflow=True)[1] for j in range(len(pairs)))
+    ctx.unload(gid)
+    for x in ids:
+        ctx.unload(x)
+    return {"workload": "64 series of 2^21-2^24 samples (random) x 64 us, each with 256-2048 "
+                        "circular templates (Porb U[3T,10T], tau U[0,3] lt-s); one CUDA graph "
+                        "over the 64 searches (4 parallel branches), launch shapes autotuned "
+                        "per length",
+            "templates": K, "value": K / (statistics.mean(ms) / 1e3), "unit": UNIT,
+            "ms_per_graph": statistics.mean(ms), "steps": steps, "warmup": warmup,
+            "autotuned": {"2^%d" % k: v for k, v in tuned.items()}, "candidates": int(ncand)}
+
+
+def run_elliptical_f16(bps, ctx, steps=2, warmup=1):
+    """Elliptical IMBH search at 2^25 samples x 128 us, 2048 five-parameter templates,
+    series stored FP16 with a power-of-two scale per 4096 samples, FP32 FFT.  Reports
+    templates/s and the whitened-power difference from the FP32-storage path on the
+    true orbits (the FP64-oracle comparison is in the GPU tests)."""
+    import torch
+    w = synth.elliptical_imbh()
+    bid = ctx.load_bank(w.bank)
+    sid16 = ctx.load_series(w.series, w.tsamp, bps.BPS_F16_SCALED)
+    prm = bps.default_params(cand_cap=1 << 22)
+    best, _ = ctx.autotune(sid16, bid, prm, sample_templates=32)
+    st = torch.cuda.Stream()
+    ms = []
+    for i in range(warmup + steps):
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        st.synchronize()
+        e0.record(st)
+        rid = ctx.search(sid16, bid, prm, stream=st)
+        e1.record(st)
+        c, total = ctx.fetch_candidates(rid, allow_overflow=True)
+        ctx.unload(rid)
+        if i >= warmup:
+            ms.append(e0.elapsed_time(e1))
+    sid32 = ctx.load_series(w.series, w.tsamp)
+    err = 0.0
+    for ti in w.true_idx:
+        a = ctx.whitened_spectrum(sid16, bid, int(ti), 1, w.n)[0]
+        b = ctx.whitened_spectrum(sid32, bid, int(ti), 1, w.n)[0]
+        err = max(err, float(np.max(np.abs(a - b) / np.maximum(1.0, b))))
+    for x in (sid16, sid32, bid):
+        ctx.unload(x)
+    K = w.bank.shape[0]
+    return {"workload": "elliptical IMBH: 2^25 samples x 128 us, %d templates (Porb U[5T,10T], "
+                        "tau U[0,20] lt-s, e U[0,0.1]), FP16 series + scale per 4096, FP32 FFT" % K,
+            "value": K / (statistics.mean(ms) / 1e3), "unit": UNIT,
+            "ms_per_step": statistics.mean(ms), "steps": steps, "warmup": warmup,
+            "autotuned": [best.log_tile, best.log_tile2, best.batch],
+            "candidates": int(total),
+            "pw_max_rel_diff_vs_fp32_storage": err}
 
 
 def config_of(w, args, ws):
@@ -434,7 +542,13 @@ def main():
 
     serving = None
     if not args.no_serving and ws == 1:
-        serving = run_serving(bps, ctx, args.serve_rate, args.serve_requests)
+        pool = serving_pool()
+        sweep = []
+        for r in [float(v) for v in args.serve_rates.split(",") if v]:
+            sweep.append(run_serving(bps, ctx, r, max(8, int(r * args.serve_seconds)), pool))
+        serving = {"workload": SERVING_WORKLOAD, "sweep": sweep}
+    uneven = run_uneven(bps, ctx) if (not args.no_uneven and ws == 1) else None
+    elliptical = run_elliptical_f16(bps, ctx) if (not args.no_elliptical and ws == 1) else None
 
     launches = sum(s["launches"] for s in stats)
     out = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": ws, "steps": args.steps,
@@ -452,7 +566,8 @@ def main():
            "stage_share": stage_share,
            "cpu_baseline": cpu, "e2e": e2e, "clocks": clk, "gpu_launches": launches,
            "candidates_per_step": ncand, "anchor_block": stats[0]["anchor_block"],
-           "serving": serving, "autotuned": tuned}
+           "serving": serving, "batched_uneven": uneven, "elliptical_f16": elliptical,
+           "autotuned": tuned}
     if rank == 0:
         print(json.dumps(out), flush=True)
     ctx.close()
