@@ -20,6 +20,12 @@ namespace bps {
 
 constexpr float kGuard = 1e-4f;
 
+// Round-to-nearest by the 1.5 * 2^23 shift: for |x| < 2^22, y = x + kRoundShift holds
+// rint(x) in its low mantissa bits, so rint(x) = y - kRoundShift (exact) and, as an
+// integer, __float_as_int(y) - kRoundBits.
+constexpr float kRoundShift = 12582912.0f;
+constexpr int kRoundBits = 0x4B400000;
+
 __device__ __forceinline__ void two_sum(float a, float b, float& s, float& e)
 {
     s = __fadd_rn(a, b);
@@ -61,17 +67,18 @@ static __device__ __noinline__ int off_round_precise(const Anchor& a, int d)
     return (int)fl + (int)floorf(v);
 }
 
-// floor(off + 1/2) - I; *precise set when the compensated branch was taken.
+// floor(off + 1/2) - I; *precise set when the compensated branch was taken.  Fast
+// path: xr = off - I - 1/2 in FP32; outside the guard band floor(xr + 1/2) = rint(xr)
+// (ties lie inside the band), taken by the shift of kRoundShift.
 __device__ __forceinline__ int off_round(const Anchor& a, int d, bool& precise)
 {
     const float df = (float)d;
-    const float inc = df * fmaf(df, fmaf(df, a.q3, a.q2), a.Lhi);
-    const float x = (a.fhi + 0.5f) - inc;
-    const float fl = floorf(x);
-    const float fr = x - fl;
-    if (fr > kGuard && fr < 1.f - kGuard) {
+    const float xr = a.fhi - df * fmaf(df, fmaf(df, a.q3, a.q2), a.Lhi);
+    const float y = __fadd_rn(xr, kRoundShift);
+    const float fr = __fsub_rn(xr, __fsub_rn(y, kRoundShift));
+    if (fabsf(fr) < 0.5f - kGuard) {
         precise = false;
-        return (int)fl;
+        return __float_as_int(y) - kRoundBits;
     }
     precise = true;
     return off_round_precise(a, d);

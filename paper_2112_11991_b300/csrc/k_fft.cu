@@ -301,17 +301,18 @@ __device__ __forceinline__ void pass1_indices(const Anchor* __restrict__ at, int
         const int ab = m >> logB;
         const float4 a4 = __ldg(reinterpret_cast<const float4*>(at + ab));
         const float q3 = __ldg(&at[ab].q3);
-        const int I = __float_as_int(a4.x);
-        const float fh = a4.y + 0.5f, L = a4.z, q2 = a4.w;
+        const int I = __float_as_int(a4.x) - kRoundBits;
+        const float fh = a4.y, L = a4.z, q2 = a4.w;
         const int d = m - ((ab << logB) + half);
 #pragma unroll
         for (int u = 0; u < 2; ++u) {
+            // xr = off - I - 1/2; outside the guard band floor(xr + 1/2) = rint(xr)
             const float df = (float)(d + u);
-            const float xx = fh - df * fmaf(df, fmaf(df, q3, q2), L);
-            const float fl = floorf(xx);
-            const float fr = xx - fl;
-            if (!(fr > kGuard && fr < 1.f - kGuard)) pm |= 1u << (2 * s + u);
-            id[2 * s + u] = m + u + I + (int)fl;
+            const float xr = fh - df * fmaf(df, fmaf(df, q3, q2), L);
+            const float y = __fadd_rn(xr, kRoundShift);
+            const float fr = __fsub_rn(xr, __fsub_rn(y, kRoundShift));
+            if (!(fabsf(fr) < 0.5f - kGuard)) pm |= 1u << (2 * s + u);
+            id[2 * s + u] = m + u + I + __float_as_int(y);
         }
     }
     if (pm) {
