@@ -281,7 +281,7 @@ __device__ __forceinline__ void pass1_last_stage(const float2* __restrict__ sm, 
 #pragma unroll
         for (int s = 0; s < RL; ++s) {
             const int k1 = j + s * Ns;
-            Yt[((int64_t)k1 << logC) + j2] = cmul(v[Radix<LOGR_LAST>::out_pos(s)], u[s]);
+            __stcs(Yt + ((int64_t)k1 << logC) + j2, cmul(v[Radix<LOGR_LAST>::out_pos(s)], u[s]));
         }
     }
 }
