@@ -7,7 +7,8 @@
   found under its true orbit at round(n T / P) for some harmonic level n.
 * 2^24 samples (8192-point column FFTs): whitened spectrum of one template.
 * 2^25 samples, the largest size (elliptical IMBH workload shape): whitened
-  spectrum and candidates of the two true orbits and one random template.
+  spectrum and candidates of the two true orbits and one random template; the same
+  with FP16 series storage against the oracle's FP32-series result.
 Tolerances: tests/gpu_common.py.
 """
 import numpy as np
@@ -105,5 +106,20 @@ def test_max_size_2p25_elliptical(bps, ctx, orc):
     for ti, p in zip(w.true_idx, w.pulsars):
         assert _recovered(gc[gc["template_idx"] == ti], T, p.period_s,
                           bps.thresholds(prm, w.n, 3)), ti
+    # the same search with FP16 series storage (scale per 4096 samples, FP32 FFT):
+    # whitened power within 5e-3 of the FP64 oracle on the FP32 series, the strongest bin
+    # of every harmonic level unchanged, each injected pulsar still found
+    s16 = ctx.load_series(w.series, w.tsamp, dtype=bps.BPS_F16_SCALED)
+    pw16 = ctx.whitened_spectrum(s16, bid, 0, 1, w.n)[0]
+    err = np.abs(pw16 - r0["Pw"]) / np.maximum(1.0, r0["Pw"])
+    assert err.max() < 5e-3, err.max()
+    S16 = ctx.harmonic_sums(s16, bid, 0, w.n)
+    for L in range(5):
+        assert int(np.argmax(S16[L])) == int(np.argmax(r0["S"][L]))
+    g16, _ = ctx.fetch_candidates(ctx.search(s16, bid, prm))
+    for ti, p in zip(w.true_idx, w.pulsars):
+        assert _recovered(g16[g16["template_idx"] == ti], T, p.period_s,
+                          bps.thresholds(prm, w.n, 3)), ti
+    ctx.unload(s16)
     ctx.unload(sid)
     ctx.unload(bid)
