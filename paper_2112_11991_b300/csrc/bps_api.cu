@@ -207,6 +207,10 @@ int make_plan(bps_ctx* ctx, const Series& s, const Bank& b, const bps_search_par
     }
     plan_geometry(p, pr.log_tile ? pr.log_tile : t1, pr.log_tile2 ? pr.log_tile2 : t2);
     p.logW = ilog2(pr.whiten_block);
+    // transposed power when a whitening block lies within one k2 (W <= R) and the warp
+    // median applies (W <= 1024): pass 2 then writes whole rows
+    p.ptrans = (pr.mode == BPS_MODE_FUSED && p.logW <= 10 && p.logW <= p.logR && p.logNP <= 6 &&
+                p.logC >= 12) ? 1 : 0;
     p.nharm = pr.nharm_max;
     p.lognh = ilog2(pr.nharm_max);
     p.nlev = p.lognh + 1;
@@ -255,7 +259,8 @@ struct Workspace {
     Anchor* anc = nullptr;
     float2* Y = nullptr;   // fused: M complex per template; plain: R2C output (M+1)
     float* x = nullptr;    // plain: resampled series
-    float* P = nullptr;
+    float* P = nullptr;    // power, then the whitened power, in bin order
+    float* Pt = nullptr;   // power in pass 2's row-major-by-k1 layout (plan.ptrans)
     float* scale = nullptr;
     char* base = nullptr;
 };
@@ -273,6 +278,7 @@ size_t ws_carve(const Plan& p, int nt, int mode, int anchor_templates, char* bas
     const size_t y = align256(sizeof(float2) * (size_t)(p.M + 1) * nt);
     const size_t x = mode == BPS_MODE_PLAIN ? align256(sizeof(float) * (size_t)p.n * nt) : 0;
     const size_t pp = align256(sizeof(float) * (size_t)p.M * nt);
+    const size_t pt = p.ptrans ? pp : 0;
     const size_t sc = align256(sizeof(float) * (size_t)(p.M >> p.logW) * nt);
     if (w) {
         char* q = base;
@@ -281,9 +287,10 @@ size_t ws_carve(const Plan& p, int nt, int mode, int anchor_templates, char* bas
         w->Y = (float2*)q; q += y;
         w->x = x ? (float*)q : nullptr; q += x;
         w->P = (float*)q; q += pp;
+        w->Pt = pt ? (float*)q : nullptr; q += pt;
         w->scale = (float*)q;
     }
-    return a + y + x + pp + sc;
+    return a + y + x + pp + pt + sc;
 }
 
 int ws_alloc(bps_ctx* ctx, const Plan& p, int nt, int mode, cudaStream_t st, Workspace& w,
@@ -355,7 +362,7 @@ int run_spectrum(bps_ctx* ctx, const Series& s, const Bank& b, const Plan& p, in
         CK(launch_pass1(v, anc, nt, p, ctx->tw, w.Y, st));
         tm.end();
         tm.begin(BPS_STAGE_PASS2);
-        CK(launch_pass2(w.Y, nt, p, ctx->tw, w.P, st));
+        CK(launch_pass2(w.Y, nt, p, ctx->tw, p.ptrans ? w.Pt : w.P, st));
         tm.end();
     } else {
         cufftHandle h;
@@ -374,7 +381,7 @@ int run_spectrum(bps_ctx* ctx, const Series& s, const Bank& b, const Plan& p, in
         tm.end();
     }
     tm.begin(BPS_STAGE_MEDIAN);
-    CK(launch_block_median(w.P, nt, p, w.scale, st));
+    CK(launch_block_median(w.P, nt, p, w.scale, st, p.ptrans ? w.Pt : nullptr));
     tm.end();
     return BPS_OK;
 }

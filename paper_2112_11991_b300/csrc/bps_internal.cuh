@@ -51,13 +51,15 @@ struct Plan {
     int nharm;      // nharm_max (power of two <= 16)
     int lognh;
     int nlev;       // log2(nharm) + 1
+    int ptrans;     // 1: pass 2 writes the power row-major by k1, P'[k1 C + k2] for bin
+                    // k1 + R k2, and the median kernel transposes it into bin order
     double tsamp;
 };
 
 // Four-step split of the packed FFT, M = R * C, with CTA tiles of 2^logTile (pass 1)
 // and 2^logTile2 (pass 2) complex values in shared memory (13: 256 threads, two CTAs
 // per SM; 14: 512 threads, one): C = 2^min(10, logM - 5) row length (pass 2),
-// R <= 2^13 column length (pass 1), G = tile1 / R adjacent columns per pass-1 CTA,
+// R <= 2^12 column length (pass 1), G = tile1 / R adjacent columns per pass-1 CTA,
 // NP = tile2 / (2C) row pairs per pass-2 CTA.
 inline void plan_geometry(Plan& p, int logTile = 14, int logTile2 = 13)
 {
@@ -65,14 +67,15 @@ inline void plan_geometry(Plan& p, int logTile = 14, int logTile2 = 13)
     p.logTile2 = logTile2;
     p.logC = p.logM - 5 < 10 ? p.logM - 5 : 10;
     p.logR = p.logM - p.logC;
-    if (p.logR > 13) {
-        p.logR = 13;
-        p.logC = p.logM - 13;
+    if (p.logR > 12) {
+        p.logR = 12;
+        p.logC = p.logM - 12;
     }
     const int lt = logTile > p.logR ? logTile : p.logR;  // a column must fit one tile
     p.logG = p.logC < lt - p.logR ? p.logC : lt - p.logR;
     p.logNP = (logTile2 - 1 - p.logC) < (p.logR - 1) ? (logTile2 - 1 - p.logC) : (p.logR - 1);
     if (p.logNP < 0) p.logNP = 0;
+    p.ptrans = 0;
 }
 
 // Anchor block length B = 2^logB: the largest (<= 2^14, <= n) for which every
@@ -131,9 +134,12 @@ cudaError_t launch_pass2(const float2* Y, int nt, const Plan& p, const float2* t
                          float* P, cudaStream_t s);
 cudaError_t launch_power_from_r2c(const float2* X, int nt, const Plan& p, float* P,
                                   cudaStream_t s);
-// finds the block medians and whitens P in place (P -> Pw); scale receives ln2/med
+// Lower median of each block of W bins and whitening into P (bin order; scale receives
+// ln2/med per block).  With p.ptrans the power is read from Pt (pass 2's
+// row-major-by-k1 layout) and the kernel transposes it; otherwise P is whitened in
+// place (Pt unused).
 cudaError_t launch_block_median(float* P, int nt, const Plan& p, float* scale,
-                                cudaStream_t s);
+                                cudaStream_t s, const float* Pt = nullptr);
 // copies the whitened spectrum left by launch_block_median (scale unused)
 cudaError_t launch_whitened(const float* P, const float* scale, int nt, const Plan& p,
                             float* out, cudaStream_t s);

@@ -92,27 +92,15 @@ __global__ void k_whitened(const float* __restrict__ Pw, Plan p, float* __restri
     out[(int64_t)tl * p.M + k] = Pw[(int64_t)tl * p.M + k];
 }
 
-// One warp per block of W = 32*VPL bins, values in registers; exact radix select of
-// the element of rank floor((W-1)/2) over four digits of the FP32 bit pattern
-// (P >= 0: sign bit 0; digits = exponent [30:23], mantissa [22:15], [14:7], [6:0])
-// with a per-warp shared histogram and a warp prefix scan, no block barrier.  The
-// block is then whitened in place: Pw = P * ln2 / med (0 when med = 0).
+// Exact lower median (element of rank floor((W-1)/2), W = 32*VPL) of the FP32 values
+// held by one warp, VPL per lane: radix select over four digits of the bit pattern
+// (values >= 0: sign bit 0; digits = exponent [30:23], mantissa [22:15], [14:7], [6:0])
+// with the warp's padded 288-word shared histogram h (bin b at b + b/8: conflict-free
+// scan reads) and a warp prefix scan, no block barrier.  Returns the median's bits.
 template <int VPL>
-__global__ void __launch_bounds__(256) k_median_warp(float* __restrict__ P, Plan p,
-                                                     float* __restrict__ scale)
+__device__ __forceinline__ uint32_t warp_lower_median(const uint32_t (&u)[VPL], uint32_t* h, int lane)
 {
-    __shared__ uint32_t hist[8][288];  // bin b at b + b/8: conflict-free scan reads
-    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-    const int tl = blockIdx.y;
-    const int64_t nblk = p.M >> p.logW;
-    const int64_t blk = (int64_t)blockIdx.x * 8 + warp;
-    if (blk >= nblk) return;
-    float* src = P + (int64_t)tl * p.M + (blk << p.logW);
-    uint32_t u[VPL];
-#pragma unroll
-    for (int i = 0; i < VPL; ++i) u[i] = __float_as_uint(src[lane + 32 * i]);
     uint32_t prefix = 0, pmask = 0, rank = (uint32_t)(32 * VPL - 1) / 2;
-    uint32_t* h = hist[warp];
 #pragma unroll
     for (int pass = 0; pass < 4; ++pass) {
         const int shift = pass == 0 ? 23 : pass == 1 ? 15 : pass == 2 ? 7 : 0;
@@ -162,12 +150,84 @@ __global__ void __launch_bounds__(256) k_median_warp(float* __restrict__ P, Plan
         rank = nrank;
         __syncwarp();
     }
-    const float med = __uint_as_float(prefix);
+    return prefix;
+}
+
+// One warp per block of W = 32*VPL bins (bin order), values in registers; the block is
+// whitened in place: Pw = P * ln2 / med (0 when med = 0).
+template <int VPL>
+__global__ void __launch_bounds__(256) k_median_warp(float* __restrict__ P, Plan p,
+                                                     float* __restrict__ scale)
+{
+    __shared__ uint32_t hist[8][288];
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    const int tl = blockIdx.y;
+    const int64_t nblk = p.M >> p.logW;
+    const int64_t blk = (int64_t)blockIdx.x * 8 + warp;
+    if (blk >= nblk) return;
+    float* src = P + (int64_t)tl * p.M + (blk << p.logW);
+    uint32_t u[VPL];
+#pragma unroll
+    for (int i = 0; i < VPL; ++i) u[i] = __float_as_uint(src[lane + 32 * i]);
+    const float med = __uint_as_float(warp_lower_median<VPL>(u, hist[warp], lane));
     const float sc = (med > 0.f) ? kLn2 / med : 0.f;
 #pragma unroll
     for (int i = 0; i < VPL; ++i) src[lane + 32 * i] = __uint_as_float(u[i]) * sc;
     if (lane == 0) scale[(int64_t)tl * nblk + blk] = sc;
 }
+
+// The same from pass 2's row-major-by-k1 power Pt[k1 C + k2] (bin k1 + R k2, W <= R):
+// a CTA of kMedCols warps takes the kMedCols blocks at k2 in [k20, k20 + kMedCols),
+// k1 in [q0, q0 + W) -- W row segments of 32 bytes -- into a shared tile padded to
+// kMedCols + 1 words per row (conflict-free column reads); warp w takes the median of
+// column k20 + w and writes its whitened block to P in bin order.  (Measured: 32-byte
+// segments with four CTAs per SM beat 128-byte segments with one.)
+constexpr int kMedCols = 8;
+constexpr int kLogMedCols = 3;
+
+template <int VPL>
+__global__ void __launch_bounds__(32 * kMedCols) k_median_warp_t(const float* __restrict__ Pt, Plan p,
+                                                                   float* __restrict__ P,
+                                                                   float* __restrict__ scale)
+{
+    constexpr int W = 32 * VPL;
+    constexpr int TS = kMedCols + 1;  // tile row stride (words)
+    extern __shared__ uint32_t tsm[];
+    uint32_t* tile = tsm;                  // W x TS
+    uint32_t* hist = tsm + W * TS;         // kMedCols x 288
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    const int tl = blockIdx.y;
+    const int lg = p.logC - kLogMedCols;  // groups of kMedCols k2 per row
+    const int k20 = (int)(blockIdx.x & ((1u << lg) - 1)) * kMedCols;
+    const int qb = (int)(blockIdx.x >> lg);
+    const int q0 = qb * W;
+    const float* src = Pt + (int64_t)tl * p.M;
+    constexpr int F4 = kMedCols / 4;  // float4 per row segment
+    for (int i = threadIdx.x; i < F4 * W; i += blockDim.x) {
+        const int r = i / F4, f = i % F4;
+        const float4 v = __ldg(reinterpret_cast<const float4*>(src + ((int64_t)(q0 + r) << p.logC) + k20 + 4 * f));
+        uint32_t* t = tile + r * TS + 4 * f;
+        t[0] = __float_as_uint(v.x);
+        t[1] = __float_as_uint(v.y);
+        t[2] = __float_as_uint(v.z);
+        t[3] = __float_as_uint(v.w);
+    }
+    __syncthreads();
+    uint32_t u[VPL];
+#pragma unroll
+    for (int i = 0; i < VPL; ++i) u[i] = tile[(lane + 32 * i) * TS + warp];
+    const float med = __uint_as_float(warp_lower_median<VPL>(u, hist + 288 * warp, lane));
+    const float sc = (med > 0.f) ? kLn2 / med : 0.f;
+    const int64_t nblk = p.M >> p.logW;
+    const int64_t blk = ((int64_t)(k20 + warp) << (p.logR - p.logW)) + qb;
+    float* dst = P + (int64_t)tl * p.M + (blk << p.logW);
+#pragma unroll
+    for (int i = 0; i < VPL; ++i) dst[lane + 32 * i] = __uint_as_float(u[i]) * sc;
+    if (lane == 0) scale[(int64_t)tl * nblk + blk] = sc;
+}
+
+template <int VPL>
+constexpr size_t med_t_smem() { return sizeof(uint32_t) * ((size_t)32 * VPL * (kMedCols + 1) + 288 * kMedCols); }
 
 // ---- TMA bulk copies into shared memory, completed on an mbarrier (inline PTX) ----
 __device__ __forceinline__ uint32_t smem_u32(const void* p)
@@ -414,10 +474,48 @@ __global__ void __launch_bounds__(kHsThreads, 2) k_harmsum(const float* __restri
 
 }  // namespace
 
+namespace {
+// Dynamic shared memory of the transposing median kernels, set once per device.
+cudaError_t med_t_attributes()
+{
+    static std::mutex mu;
+    static bool done[64] = {};
+    int dev = 0;
+    cudaError_t e = cudaGetDevice(&dev);
+    if (e != cudaSuccess) return e;
+    if (dev < 0 || dev >= 64) return cudaErrorInvalidDevice;
+    std::lock_guard<std::mutex> lk(mu);
+    if (done[dev]) return cudaSuccess;
+#define BPS_MED_ATTR(v) \
+    if (e == cudaSuccess)  \
+        e = cudaFuncSetAttribute(k_median_warp_t<v>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)med_t_smem<v>());
+    BPS_MED_ATTR(1) BPS_MED_ATTR(2) BPS_MED_ATTR(4) BPS_MED_ATTR(8) BPS_MED_ATTR(16) BPS_MED_ATTR(32)
+#undef BPS_MED_ATTR
+    if (e == cudaSuccess) done[dev] = true;
+    return e;
+}
+}  // namespace
+
 cudaError_t launch_block_median(float* P, int nt, const Plan& p, float* scale,
-                                cudaStream_t s)
+                                cudaStream_t s, const float* Pt)
 {
     const int64_t nblk = p.M >> p.logW;
+    if (p.ptrans) {
+        if (!Pt || p.logW > 10 || p.logW > p.logR || p.logC < kLogMedCols) return cudaErrorInvalidValue;
+        cudaError_t e = med_t_attributes();
+        if (e != cudaSuccess) return e;
+        dim3 tgrid((unsigned)(nblk / kMedCols), (unsigned)nt);
+        const int th = 32 * kMedCols;
+        switch (p.logW) {
+            case 5: k_median_warp_t<1><<<tgrid, th, med_t_smem<1>(), s>>>(Pt, p, P, scale); break;
+            case 6: k_median_warp_t<2><<<tgrid, th, med_t_smem<2>(), s>>>(Pt, p, P, scale); break;
+            case 7: k_median_warp_t<4><<<tgrid, th, med_t_smem<4>(), s>>>(Pt, p, P, scale); break;
+            case 8: k_median_warp_t<8><<<tgrid, th, med_t_smem<8>(), s>>>(Pt, p, P, scale); break;
+            case 9: k_median_warp_t<16><<<tgrid, th, med_t_smem<16>(), s>>>(Pt, p, P, scale); break;
+            default: k_median_warp_t<32><<<tgrid, th, med_t_smem<32>(), s>>>(Pt, p, P, scale); break;
+        }
+        return cudaGetLastError();
+    }
     dim3 wgrid((unsigned)((nblk + 7) / 8), (unsigned)nt);
     switch (p.logW) {
         case 5: k_median_warp<1><<<wgrid, 256, 0, s>>>(P, p, scale); break;

@@ -422,6 +422,11 @@ __global__ void __launch_bounds__(1024, 1) k_pass2(const float2* __restrict__ Y,
     // slack in all).  The first radix-16 stage (Ns = 1) is fused with the load:
     // butterfly (line, j) reads elements j + s C/16 of its row straight from Y.
     const int skew = logNP <= 4 ? (16 >> logNP) : (logNP == 5 ? 1 : 0);
+    // W_N^q of the NP low rows, for the row-major power layout (plan.ptrans, NP <= 64);
+    // visible to all after the first-stage barrier
+    __shared__ float2 s_wq[64];
+    if (p.ptrans && (int)threadIdx.x < NP)
+        s_wq[threadIdx.x] = twiddle((uint32_t)(q0 + threadIdx.x), logn);
     const int logQ = logC - 4;
     constexpr int BPT1 = kEPT2 / 16;
 #pragma unroll
@@ -452,6 +457,46 @@ __global__ void __launch_bounds__(1024, 1) k_pass2(const float2* __restrict__ Y,
         else if (rem == 1) fft_stage<1, kEPT2, false>(sm, logC, logNs, logNP + 1, C, 1, skew, tw);
     }
     float* Pt = P + (int64_t)tl * M;
+    if (p.ptrans) {
+        // row-major power: P'[q C + k2] holds bin q + R k2.  Items k2-fastest, so a warp
+        // reads consecutive elements of one line and writes consecutive words of a row.
+        const int twsh = 12 - logC;
+        const int items = NP * C;
+        for (int it = threadIdx.x; it < items; it += nthr) {
+            const int ql = it >> logC, k2 = it & (C - 1);
+            const int q = q0 + ql;
+            const int lowl = ql, highl = NP + ql;
+            const int lo0 = lowl * skew, hi0 = highl * skew;
+            float pa, pb;
+            if (q != 0) {
+                const float2 w = cmul(s_wq[ql], __ldg(tw + (k2 << twsh)));
+                power_pair(sm[pad(lowl * C + k2) + lo0], sm[pad(highl * C + (C - 1 - k2)) + hi0], w,
+                           pa, pb);
+                Pt[((int64_t)q << logC) + k2] = pa;
+                Pt[((int64_t)(R - q) << logC) + (C - 1 - k2)] = pb;
+            } else {
+                if (k2 <= (C >> 1)) {  // row 0: bins R k2 and M - R k2 = R (C - k2)
+                    power_pair(sm[pad(k2) + lo0], sm[pad((C - k2) & (C - 1)) + lo0],
+                               __ldg(tw + (k2 << twsh)), pa, pb);
+                    if (k2 == 0) {
+                        Pt[0] = 0.f;
+                    } else {
+                        Pt[k2] = pa;
+                        if (k2 != (C >> 1)) Pt[C - k2] = pb;
+                    }
+                }
+                if (k2 < (C >> 1)) {  // row R/2: bins R/2 + R k2 and R/2 + R (C - 1 - k2)
+                    const float2 w =
+                        cmul(twiddle((uint32_t)(R >> 1), logn), __ldg(tw + (k2 << twsh)));
+                    power_pair(sm[pad(highl * C + k2) + hi0],
+                               sm[pad(highl * C + (C - 1 - k2)) + hi0], w, pa, pb);
+                    Pt[((int64_t)(R >> 1) << logC) + k2] = pa;
+                    Pt[((int64_t)(R >> 1) << logC) + (C - 1 - k2)] = pb;
+                }
+            }
+        }
+        return;
+    }
     // W_N^{q + R k2} = W_N^q * W_{2C}^{k2};  W_{2C}^{k2} = tw[k2 * 8192 / (2C)]
     const int ql = threadIdx.x & (NP - 1);
     const int q = q0 + ql;
@@ -516,11 +561,11 @@ using Pass1Fn = void (*)(SeriesView, const Anchor*, Plan, const float2*, float2*
 using Pass2Fn = void (*)(const float2*, Plan, const float2*, float*);
 
 #define BPS_PASS1_GEOMETRIES(X) \
-    X(10, 10, 4) X(10, 10, 3) X(11, 10, 3) X(11, 10, 2) X(12, 10, 2) X(12, 10, 1) X(13, 10, 1) \
-    X(13, 10, 0) X(13, 11, 1) X(13, 11, 0) X(-1, -1, -1)
+    X(10, 10, 4) X(10, 10, 3) X(11, 10, 3) X(11, 10, 2) X(12, 10, 2) X(12, 10, 1) X(12, 11, 2) \
+    X(12, 11, 1) X(12, 12, 2) X(12, 12, 1) X(-1, -1, -1)
 #define BPS_PASS2_GEOMETRIES(X) \
-    X(10, 10, 2) X(10, 10, 3) X(11, 10, 2) X(11, 10, 3) X(12, 10, 2) X(12, 10, 3) X(13, 10, 2) \
-    X(13, 10, 3) X(13, 11, 1) X(13, 11, 2) X(-1, -1, -1)
+    X(10, 10, 2) X(10, 10, 3) X(11, 10, 2) X(11, 10, 3) X(12, 10, 2) X(12, 10, 3) X(12, 11, 1) \
+    X(12, 11, 2) X(12, 12, 0) X(12, 12, 1) X(-1, -1, -1)
 
 Pass1Fn pick_pass1(const Plan& p)
 {
