@@ -58,9 +58,9 @@ struct Plan {
 
 // Four-step split of the packed FFT, M = R * C, with CTA tiles of 2^logTile (pass 1)
 // and 2^logTile2 (pass 2) complex values in shared memory (13: 256 threads, two CTAs
-// per SM; 14: 512 threads, one): C = 2^min(10, logM - 5) row length (pass 2),
-// R <= 2^12 column length (pass 1), G = tile1 / R adjacent columns per pass-1 CTA,
-// NP = tile2 / (2C) row pairs per pass-2 CTA.
+// per SM; 14: 512 threads, one): C = 2^min(10, logM - 5) row length (pass 2), raised
+// to M / 2^12 where R would exceed 2^12 column length (pass 1); G = tile1 / R adjacent
+// columns per pass-1 CTA, NP = tile2 / (2C) row pairs per pass-2 CTA.
 inline void plan_geometry(Plan& p, int logTile = 14, int logTile2 = 13)
 {
     p.logTile = logTile;

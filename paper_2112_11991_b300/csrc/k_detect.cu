@@ -178,12 +178,13 @@ __global__ void __launch_bounds__(256) k_median_warp(float* __restrict__ P, Plan
 
 // The same from pass 2's row-major-by-k1 power Pt[k1 C + k2] (bin k1 + R k2, W <= R):
 // a CTA of kMedCols warps takes the kMedCols blocks at k2 in [k20, k20 + kMedCols),
-// k1 in [q0, q0 + W) -- W row segments of 32 bytes -- into a shared tile padded to
+// k1 in [q0, q0 + W) -- W row segments of 64 bytes -- into a shared tile padded to
 // kMedCols + 1 words per row (conflict-free column reads); warp w takes the median of
-// column k20 + w and writes its whitened block to P in bin order.  (Measured: 32-byte
-// segments with four CTAs per SM beat 128-byte segments with one.)
-constexpr int kMedCols = 8;
-constexpr int kLogMedCols = 3;
+// column k20 + w and writes its whitened block to P in bin order.  (Measured at
+// C = 4096: 64-byte segments with two CTAs per SM beat 32-byte segments with four and
+// 128-byte segments with one.)
+constexpr int kMedCols = 16;
+constexpr int kLogMedCols = 4;
 
 template <int VPL>
 __global__ void __launch_bounds__(32 * kMedCols) k_median_warp_t(const float* __restrict__ Pt, Plan p,
