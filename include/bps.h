@@ -229,6 +229,52 @@ int bps_graph_launch(bps_ctx* ctx, int64_t graph_id, void* cuda_stream);
 int bps_graph_fetch(bps_ctx* ctx, int64_t graph_id, int64_t pair, bps_candidate* out, int64_t cap,
                     int64_t* n_written, int64_t* n_total);
 
+/* ---- random template banks from the parameter-space metric (host routines) ------ */
+
+/* Search region and bank requirements (Sec. 2.3-2.4; defaults = Table 1).  Circular
+ * orbits (3 orbital coordinates tau, Omega, alpha) when ecc_max = 0, elliptical (adds
+ * omega, e) otherwise. */
+typedef struct {
+    double tobs_s;            /* observation length T                                      */
+    double f_max_hz;          /* spin frequency the metric is projected at (f_max)         */
+    double mismatch;          /* nominal mismatch m* (0, 1)                                */
+    double coverage;          /* coverage eta (0, 1)                                       */
+    double porb_min_s, porb_max_s;  /* P_orb uniform prior                                */
+    double tau_max_lts;       /* > 0: tau uniform in [0, tau_max_lts]; 0: tau in
+                                 [0, tau_max(P_orb)] from Kepler's third law and the masses */
+    double m_pulsar_min_msun; /* lightest pulsar (Kepler bound)                            */
+    double m_comp_max_msun;   /* heaviest companion (Kepler bound)                         */
+    double ecc_max;           /* e uniform in [0, ecc_max]; 0 = circular                   */
+    int32_t n_time;           /* midpoint-rule points for the time averages (>= 16)        */
+    int32_t n_volume;         /* Monte Carlo points for the proper volume (>= 100)         */
+} bps_bank_spec;
+
+/* Table 1 values: T = 1.2 h, f_max = 66.67 Hz, m* = 0.2, eta = 0.9, P_orb U(6, 12) h,
+ * m_p,min = 1.4, m_c,max = 8 Msun, e U(0, 0.1), n_time 256, n_volume 20000. */
+void bps_default_bank_spec(bps_bank_spec* spec);
+
+/* sqrt(det gamma) of the frequency-projected metric (Sec. 2.4: gamma_ab = g_ab -
+ * g_fa g_fb / g_ff, g_ab = <d_a Phi d_b Phi> - <d_a Phi><d_b Phi> over [0, T], Phi =
+ * 2 pi f_max (t - Delta_R)) at each of `count` templates, in the orbital coordinates
+ * (tau [lt-s], Omega [rad/s], alpha[, omega, e]).  BPS_ERR_INVALID_ARG on a bad spec
+ * or template. */
+int bps_metric_density(const bps_bank_spec* spec, const bps_template* t, int64_t count,
+                       double* sqrt_det_out);
+
+/* The projected metric itself at one template: n x n row-major into gamma_out (n = 3
+ * circular, 5 elliptical). */
+int bps_metric_projected(const bps_bank_spec* spec, const bps_template* t, double* gamma_out);
+
+/* Random template bank (Sec. 2.4, "Random Template Banks"): proper volume V of the prior
+ * region by Monte Carlo, N_R = ln(1 - eta) / ln(1 - m*^(n/2) C_n / V) templates drawn
+ * with density proportional to sqrt(det gamma) (rejection sampling, seeded).  Writes
+ * ceil(N_R) templates to out (*n_out = that count; BPS_ERR_CAND_OVERFLOW and nothing
+ * written if it exceeds cap; out = NULL with cap = 0 computes the count only),
+ * *proper_volume = V, *n_expected = N_R (either may be NULL).  Host threads evaluate
+ * the densities; the result is deterministic for a given seed and spec. */
+int bps_metric_bank(const bps_bank_spec* spec, uint64_t seed, bps_template* out, int64_t cap,
+                    int64_t* n_out, double* proper_volume, double* n_expected);
+
 /* Candidate distillation (App. A: repeated detections of one candidate are grouped).
  * Host routine, no device work.  Each candidate's fundamental frequency is
  * f = bin / (nharm T), T = n_samples t_samp, and its significance the false-alarm

@@ -10,6 +10,9 @@ Paper anchors (arXiv:2112.11991): Kepler's equation and the detection
 statistic (Sec. 2.1), the BT Roemer delay and Algorithm 1 (App. A),
 the incoherent harmonic sum and its chi^2 statistics (Sec. 2.1).
 
+``oracle/metric.py`` evaluates the template-bank metric (Sec. 2.3-2.4) at 40 digits
+with numerically differentiated phase, for the tests of the bank generator.
+
 Parity pinned by ``tests/test_oracle_*.py`` against closed forms, brute force
 and the paper's printed App. B coefficients; the whitening rule, harmonic bin
 map, threshold statistic and out-of-range fill are readings of the paper

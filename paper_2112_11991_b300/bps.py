@@ -40,7 +40,8 @@ EXPORTED = ["bps_default_params", "bps_create", "bps_destroy", "bps_load_series"
             "bps_request_stats", "bps_whitened_spectrum_noalloc", "bps_server_create",
             "bps_server_destroy", "bps_server_submit", "bps_server_result", "bps_server_stats",
             "bps_server_last_error", "bps_autotune", "bps_distill", "bps_series_update",
-            "bps_graph_create", "bps_graph_launch", "bps_graph_fetch"]
+            "bps_graph_create", "bps_graph_launch", "bps_graph_fetch", "bps_default_bank_spec",
+            "bps_metric_density", "bps_metric_projected", "bps_metric_bank"]
 STAGES = ["anchors", "pass1", "pass2", "power", "median", "harmsum"]
 
 
@@ -58,6 +59,14 @@ class bps_template(C.Structure):
 class bps_candidate(C.Structure):
     _fields_ = [("template_idx", C.c_uint32), ("nharm", C.c_uint16), ("flags", C.c_uint16),
                 ("bin", C.c_uint32), ("power", C.c_float)]
+
+
+class bps_bank_spec(C.Structure):
+    _fields_ = [("tobs_s", C.c_double), ("f_max_hz", C.c_double), ("mismatch", C.c_double),
+                ("coverage", C.c_double), ("porb_min_s", C.c_double), ("porb_max_s", C.c_double),
+                ("tau_max_lts", C.c_double), ("m_pulsar_min_msun", C.c_double),
+                ("m_comp_max_msun", C.c_double), ("ecc_max", C.c_double), ("n_time", C.c_int32),
+                ("n_volume", C.c_int32)]
 
 
 class bps_search_params(C.Structure):
@@ -158,6 +167,15 @@ def lib():
         L.bps_graph_launch.argtypes = [vp, i64, vp]
         L.bps_graph_fetch.restype = i32
         L.bps_graph_fetch.argtypes = [vp, i64, i64, vp, i64, P(i64), P(i64)]
+        L.bps_default_bank_spec.restype = None
+        L.bps_default_bank_spec.argtypes = [P(bps_bank_spec)]
+        L.bps_metric_density.restype = i32
+        L.bps_metric_density.argtypes = [P(bps_bank_spec), vp, i64, vp]
+        L.bps_metric_projected.restype = i32
+        L.bps_metric_projected.argtypes = [P(bps_bank_spec), vp, vp]
+        L.bps_metric_bank.restype = i32
+        L.bps_metric_bank.argtypes = [P(bps_bank_spec), C.c_uint64, vp, i64, P(i64),
+                                      P(C.c_double), P(C.c_double)]
         _lib = L
     return _lib
 
@@ -196,6 +214,59 @@ def distill(cands: np.ndarray, n_samples: int, tsamp: float, tol_bins: float = 1
     if rc:
         raise BpsError(rc, "bps_distill: invalid arguments")
     return out[:n.value]
+
+
+def default_bank_spec(**kw) -> bps_bank_spec:
+    """Template-bank search region (Table 1 defaults), fields overridden by keyword."""
+    sp = bps_bank_spec()
+    lib().bps_default_bank_spec(C.byref(sp))
+    for k, v in kw.items():
+        if not hasattr(sp, k):
+            raise TypeError("unknown bank spec field %r" % k)
+        setattr(sp, k, v)
+    return sp
+
+
+def _bank_array(bank) -> np.ndarray:
+    return np.ascontiguousarray(np.asarray(bank, np.float64).reshape(-1, 5))
+
+
+def metric_density(spec: bps_bank_spec, bank) -> np.ndarray:
+    """sqrt(det) of the frequency-projected metric at each template (K x 5 array)."""
+    b = _bank_array(bank)
+    out = np.zeros(b.shape[0], np.float64)
+    rc = lib().bps_metric_density(C.byref(spec), _np_ptr(b), b.shape[0], _np_ptr(out))
+    if rc:
+        raise BpsError(rc, "bps_metric_density: invalid spec or template")
+    return out
+
+
+def metric_projected(spec: bps_bank_spec, template) -> np.ndarray:
+    """The frequency-projected metric (n x n, n = 3 circular / 5 elliptical) at one template."""
+    b = _bank_array(template)
+    n = 5 if spec.ecc_max > 0 else 3
+    out = np.zeros((n, n), np.float64)
+    rc = lib().bps_metric_projected(C.byref(spec), _np_ptr(b), _np_ptr(out))
+    if rc:
+        raise BpsError(rc, "bps_metric_projected: invalid spec or template")
+    return out
+
+
+def metric_bank(spec: bps_bank_spec, seed: int = 0, cap: int = 1 << 22, count_only=False):
+    """Random template bank of the region (bps_metric_bank): returns (bank K x 5 array,
+    proper volume, expected template count N_R); count_only skips drawing the bank."""
+    n = C.c_int64()
+    vol, nexp = C.c_double(), C.c_double()
+    out = np.zeros((0 if count_only else cap, 5), np.float64)
+    rc = lib().bps_metric_bank(C.byref(spec), int(seed), None if count_only else _np_ptr(out),
+                               0 if count_only else cap, C.byref(n), C.byref(vol), C.byref(nexp))
+    if count_only and not rc:
+        return out, vol.value, nexp.value
+    if rc:
+        raise BpsError(rc, "bps_metric_bank: %s" % ("bank of %d templates exceeds cap" % n.value
+                                                    if rc == BPS_ERR_CAND_OVERFLOW else
+                                                    "invalid spec"))
+    return out[:n.value].copy(), vol.value, nexp.value
 
 
 def thresholds(params: bps_search_params, n_samples: int, n_templates: int) -> np.ndarray:
@@ -560,6 +631,22 @@ def bps_set_profiling(ctx, on):
     return lib().bps_set_profiling(ctx, on)
 
 
+def bps_default_bank_spec(spec):
+    return lib().bps_default_bank_spec(spec)
+
+
+def bps_metric_density(spec, t, count, out):
+    return lib().bps_metric_density(spec, t, count, out)
+
+
+def bps_metric_projected(spec, t, out):
+    return lib().bps_metric_projected(spec, t, out)
+
+
+def bps_metric_bank(spec, seed, out, cap, n_out, vol, nexp):
+    return lib().bps_metric_bank(spec, seed, out, cap, n_out, vol, nexp)
+
+
 def bps_series_update(ctx, sid, data, on_device):
     return lib().bps_series_update(ctx, sid, data, on_device)
 
@@ -580,6 +667,7 @@ def bps_request_stats(ctx, rid, out):
     return lib().bps_request_stats(ctx, rid, out)
 
 
-__all__ = ["Context", "Server", "distill", "bps_server_config", "BpsError", "default_params", "thresholds", "CAND_DTYPE", "EXPORTED",
+__all__ = ["Context", "Server", "distill", "bps_server_config", "bps_bank_spec",
+           "default_bank_spec", "metric_density", "metric_projected", "metric_bank", "BpsError", "default_params", "thresholds", "CAND_DTYPE", "EXPORTED",
            "STAGES", "bps_template", "bps_candidate", "bps_search_params", "bps_stats"] + EXPORTED + [
     n for n in dir() if n.startswith("BPS_")]
