@@ -59,7 +59,7 @@ def parse():
                          "scale per 4096 samples (FFT arithmetic is FP32 either way)")
     ap.add_argument("--no-plain", action="store_true")
     ap.add_argument("--no-serving", action="store_true")
-    ap.add_argument("--serve-rates", default="1,5,20,50",
+    ap.add_argument("--serve-rates", default="1,2,5,10,20,50",
                     help="Poisson request rates (req/s) of the serving sweep")
     ap.add_argument("--serve-seconds", type=float, default=4.0,
                     help="arrival window per rate (requests = max(8, rate x seconds))")
@@ -239,8 +239,10 @@ def run_reference(args, ws, rank):
 
 
 def serving_pool(seed=5):
-    """Seeded series for the serving sweep: three per length 2^20..2^24 at 64 us."""
-    return {logn: [synth.noise(1 << logn, 3000 + 10 * logn + i) for i in range(3)]
+    """Seeded series for the serving sweep: three per length 2^20..2^24 at 64 us, the
+    first with one injected pulsar-BH binary (0-1 pulsar per request)."""
+    return {logn: [synth.pulsar_bh_series(1 << logn, 64e-6, 3000 + 10 * logn)[0]] +
+            [synth.noise(1 << logn, 3000 + 10 * logn + i) for i in (1, 2)]
             for logn in range(20, 25)}
 
 
@@ -294,7 +296,8 @@ def run_serving(bps, ctx, rate, nreq, pool, seed=5):
             "p99_ms": 1e3 * float(np.percentile(lat, 99))}
 
 
-SERVING_WORKLOAD = ("Poisson arrivals; series 2^20-2^24 (log-uniform) x 64 us, FP16 storage; "
+SERVING_WORKLOAD = ("Poisson arrivals; series 2^20-2^24 (log-uniform) x 64 us, FP16 storage, "
+                    "one in three with an injected pulsar-BH binary; "
                     "banks 64-4096 (log-uniform) circular or elliptical (e <= 0.1) templates; "
                     "server max_active 4, 2 launch groups in flight per request, HBM budget "
                     "0.9 x free; latency from submission to candidates on the host")
@@ -302,23 +305,29 @@ SERVING_WORKLOAD = ("Poisson arrivals; series 2^20-2^24 (log-uniform) x 64 us, F
 
 def run_uneven(bps, ctx, steps=2, warmup=1, seed=11):
     """Batched uneven search: 64 series of random length 2^21..2^24 at 64 us, each with
-    its own bank of 256..2048 circular templates (Porb U[3T,10T], tau U[0,3] lt-s, phi
-    U), launch shapes autotuned per length, all 64 searches captured in one CUDA graph and
-    replayed; device time per replay by CUDA events on the launching stream."""
+    one injected pulsar-BH binary (as in the 2^23 workload) and its own bank of
+    256..2048 circular templates (Porb U[3T,10T], tau U[0,3] lt-s, phi U) that includes
+    the true orbit; launch shapes autotuned per length, all 64 searches captured in one
+    CUDA graph and replayed; device time per replay by CUDA events on the launching
+    stream.  Also counts the pulsars whose true template has a candidate within one bin
+    of n T / P at some harmonic level n."""
     import torch
     rng = np.random.default_rng(seed)
-    pairs, K, n_of = [], 0, {}
+    pairs, K, n_of, truth = [], 0, {}, []
     ids = []
     for i in range(64):
         logn = int(rng.integers(21, 25))
         n, ts = 1 << logn, 64e-6
         T = n * ts
         k = int(rng.integers(256, 2049))
-        bank, _ = synth.uniform_bank(k, 5000 + i, (3 * T, 10 * T), (0.0, 3.0))
-        sid = ctx.load_series(synth.noise(n, 6000 + i), ts)
+        x, p = synth.pulsar_bh_series(n, ts, 6000 + i)
+        bank, where = synth.uniform_bank(k, 5000 + i, (3 * T, 10 * T), (0.0, 3.0),
+                                         true_orbits=[p.orbit()])
+        sid = ctx.load_series(x, ts)
         bid = ctx.load_bank(bank)
         ids += [sid, bid]
         pairs.append((sid, bid))
+        truth.append((where[0], T, p.period_s))
         n_of[logn] = (sid, bid)
         K += k
     prm = bps.default_params(cand_cap=1 << 20)
@@ -338,17 +347,23 @@ def run_uneven(bps, ctx, steps=2, warmup=1, seed=11):
         st.synchronize()
         if i >= warmup:
             ms.append(e0.elapsed_time(e1))
-    ncand = sum(ctx.graph_fetch(gid, j, allow_overflow=True)[1] for j in range(len(pairs)))
+    ncand, found = 0, 0
+    for j, (ti, T, P) in enumerate(truth):
+        c, tot = ctx.graph_fetch(gid, j, allow_overflow=True)
+        ncand += tot
+        c = c[c["template_idx"] == ti]
+        found += any(abs(int(b) - round(int(h) * T / P)) <= 1 for b, h in zip(c["bin"], c["nharm"]))
     ctx.unload(gid)
     for x in ids:
         ctx.unload(x)
-    return {"workload": "64 series of 2^21-2^24 samples (random) x 64 us, each with 256-2048 "
-                        "circular templates (Porb U[3T,10T], tau U[0,3] lt-s); one CUDA graph "
-                        "over the 64 searches (4 parallel branches), launch shapes autotuned "
-                        "per length",
+    return {"workload": "64 series of 2^21-2^24 samples (random) x 64 us, one injected pulsar-BH "
+                        "binary each, each with 256-2048 circular templates (Porb U[3T,10T], "
+                        "tau U[0,3] lt-s) including its true orbit; one CUDA graph over the 64 "
+                        "searches (4 parallel branches), launch shapes autotuned per length",
             "templates": K, "value": K / (statistics.mean(ms) / 1e3), "unit": UNIT,
             "ms_per_graph": statistics.mean(ms), "steps": steps, "warmup": warmup,
-            "autotuned": {"2^%d" % k: v for k, v in tuned.items()}, "candidates": int(ncand)}
+            "autotuned": {"2^%d" % k: v for k, v in tuned.items()}, "candidates": int(ncand),
+            "pulsars_found": "%d of 64" % found}
 
 
 def run_elliptical_f16(bps, ctx, steps=2, warmup=1):

@@ -228,6 +228,21 @@ def htru_circular(n: int = 1 << 23, K: int = 4096, seed: int = 2, with_series=Tr
     return w
 
 
+def pulsar_bh_series(n: int, tsamp: float, seed: int, amp: float = 0.02):
+    """N(0,1) series with one pulsar-BH binary drawn as in htru_circular (P U[20,100] ms,
+    m_c 10 Msun, Porb U[3T,10T], tau = tau_max sin i).  Returns (series, Pulsar)."""
+    T = n * tsamp
+    rng = np.random.default_rng(seed + 700)
+    porb = rng.uniform(3 * T, 10 * T)
+    cosi = rng.uniform(0.0, 1.0)
+    p = Pulsar(period_s=rng.uniform(0.020, 0.100), porb_s=porb,
+               tau_lts=float(tau_max(porb, 1.4, 10.0)) * math.sqrt(1.0 - cosi * cosi),
+               phi_rad=rng.uniform(0.0, TWO_PI), amp=amp)
+    x = noise(n, seed)
+    inject(x, tsamp, p)
+    return x, p
+
+
 def elliptical_imbh(n: int = 1 << 25, K: int = 2048, seed: int = 3, with_series=True,
                     amp: float = 0.02) -> Workload:
     """Elliptical IMBH-in-globular-cluster: 2^25 samples at 128 us, 2 pulsars with
