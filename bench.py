@@ -83,10 +83,14 @@ def peaks():
 
 
 def kernel_source_hash():
+    """Hash of the device-kernel sources (csrc/k_*.cu and the headers they include), the
+    code the committed ncu traffic was captured on."""
     h = hashlib.sha256()
-    for f in sorted(os.listdir(os.path.join(ROOT, "paper_2112_11991_b300", "csrc"))):
-        with open(os.path.join(ROOT, "paper_2112_11991_b300", "csrc", f), "rb") as fh:
-            h.update(fh.read())
+    d = os.path.join(ROOT, "paper_2112_11991_b300", "csrc")
+    for f in sorted(os.listdir(d)):
+        if (f.startswith("k_") and f.endswith(".cu")) or f.endswith(".cuh"):
+            with open(os.path.join(d, f), "rb") as fh:
+                h.update(fh.read())
     return h.hexdigest()[:16]
 
 
