@@ -915,6 +915,7 @@ int bps_graph_create(bps_ctx* ctx, int64_t count, const int64_t* series_ids,
         return fail(ctx, BPS_ERR_UNSUPPORTED, "graphs capture the fused form only");
     CK(cudaSetDevice(ctx->device));
     CK(set_smem_attributes());
+    CK(prepare_detect_kernels());
     const int B = (int)std::min<int64_t>(kGraphBranches, count);
     std::vector<Series*> ss((size_t)count);
     std::vector<Bank*> bb((size_t)count);

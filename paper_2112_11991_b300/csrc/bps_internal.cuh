@@ -128,6 +128,9 @@ cudaError_t launch_index_map(const Anchor* anc, const Plan& p, int32_t* idx,
 cudaError_t launch_resample(const SeriesView& x, const Anchor* anc, int nt, const Plan& p,
                             float* out, cudaStream_t s);
 cudaError_t set_smem_attributes();
+// Function attributes and occupancy of the median and harmonic-sum kernels, once per
+// device (host-side only; called before a graph capture so none happens during one).
+cudaError_t prepare_detect_kernels();
 cudaError_t launch_pass1(const SeriesView& x, const Anchor* anc, int nt, const Plan& p,
                          const float2* tw, float2* Y, cudaStream_t s);
 cudaError_t launch_pass2(const float2* Y, int nt, const Plan& p, const float2* tw,

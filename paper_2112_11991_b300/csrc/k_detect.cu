@@ -604,4 +604,16 @@ cudaError_t launch_harmsum(const float* P, const float* scale, int nt, int64_t t
     }
 }
 
+cudaError_t prepare_detect_kernels()
+{
+    int c = 0;
+    cudaError_t e = med_t_attributes();
+    if (e == cudaSuccess) e = hs_shape<1>(c);
+    if (e == cudaSuccess) e = hs_shape<2>(c);
+    if (e == cudaSuccess) e = hs_shape<4>(c);
+    if (e == cudaSuccess) e = hs_shape<8>(c);
+    if (e == cudaSuccess) e = hs_shape<16>(c);
+    return e;
+}
+
 }  // namespace bps
