@@ -84,7 +84,9 @@ def test_2p24_whitened_spectrum(bps, ctx, orc):
     pw = ctx.whitened_spectrum(sid, bid, 0, 1, n)
     _, res = oracle_on_gpu_maps(ctx, orc, sid, bid, x, ts, np.array([p.orbit()]),
                                 want_arrays=True)
-    assert pw_close(pw[0], res[0]["Pw"]) <= PW_TOL
+    e = pw_close(pw[0], res[0]["Pw"])
+    print("\n[error] 2^24 FP32 whitened power vs FP64 oracle: %.3g" % e)
+    assert e <= PW_TOL
     ctx.unload(sid)
     ctx.unload(bid)
 
@@ -100,7 +102,9 @@ def test_max_size_2p25_elliptical(bps, ctx, orc):
                                  want_arrays=False)
     r0 = orc.search_template(w.series, w.tsamp, w.bank[0], want_arrays=True,
                              idx_in=ctx.index_map(sid, bid, 0, w.n)[0].astype(np.int64))
-    assert pw_close(pw[0], r0["Pw"]) <= PW_TOL
+    e32 = pw_close(pw[0], r0["Pw"])
+    print("\n[error] 2^25 FP32 whitened power vs FP64 oracle: %.3g" % e32)
+    assert e32 <= PW_TOL
     compare_candidates(gc, oc, bps.thresholds(prm, w.n, w.bank.shape[0]))
     T = w.n * w.tsamp
     for ti, p in zip(w.true_idx, w.pulsars):
@@ -112,8 +116,12 @@ def test_max_size_2p25_elliptical(bps, ctx, orc):
     s16 = ctx.load_series(w.series, w.tsamp, dtype=bps.BPS_F16_SCALED)
     pw16 = ctx.whitened_spectrum(s16, bid, 0, 1, w.n)[0]
     err = np.abs(pw16 - r0["Pw"]) / np.maximum(1.0, r0["Pw"])
+    print("[error] 2^25 FP16-storage whitened power vs FP64 oracle: %.3g" % err.max())
     assert err.max() < 5e-3, err.max()
     S16 = ctx.harmonic_sums(s16, bid, 0, w.n)
+    sig = [float(np.max(np.abs(S16[L] - r0["S"][L]) / ((1 << L) + r0["S"][L]))) for L in range(5)]
+    print("[error] 2^25 FP16-storage harmonic sums vs FP64 oracle, |dS|/(n+S) per level: %s"
+          % ", ".join("%.2g" % v for v in sig))
     for L in range(5):
         assert int(np.argmax(S16[L])) == int(np.argmax(r0["S"][L]))
     g16, _ = ctx.fetch_candidates(ctx.search(s16, bid, prm))
