@@ -271,7 +271,8 @@ int bps_metric_projected(const bps_bank_spec* spec, const bps_template* t, doubl
  * ceil(N_R) templates to out (*n_out = that count; BPS_ERR_CAND_OVERFLOW and nothing
  * written if it exceeds cap; out = NULL with cap = 0 computes the count only),
  * *proper_volume = V, *n_expected = N_R (either may be NULL).  Host threads evaluate
- * the densities; the result is deterministic for a given seed and spec. */
+ * the densities; the result is deterministic for a given seed and spec.
+ * BPS_ERR_OUT_OF_MEMORY if host memory or threads cannot be had. */
 int bps_metric_bank(const bps_bank_spec* spec, uint64_t seed, bps_template* out, int64_t cap,
                     int64_t* n_out, double* proper_volume, double* n_expected);
 

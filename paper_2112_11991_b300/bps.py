@@ -252,20 +252,28 @@ def metric_projected(spec: bps_bank_spec, template) -> np.ndarray:
     return out
 
 
-def metric_bank(spec: bps_bank_spec, seed: int = 0, cap: int = 1 << 22, count_only=False):
+def metric_bank(spec: bps_bank_spec, seed: int = 0, cap: int = 1 << 24, count_only=False):
     """Random template bank of the region (bps_metric_bank): returns (bank K x 5 array,
-    proper volume, expected template count N_R); count_only skips drawing the bank."""
+    proper volume, expected template count N_R); count_only skips drawing the bank.  The
+    count is computed first (the same seed gives the same volume), then exactly that many
+    rows are allocated; more than cap templates raises BPS_ERR_CAND_OVERFLOW."""
     n = C.c_int64()
     vol, nexp = C.c_double(), C.c_double()
-    out = np.zeros((0 if count_only else cap, 5), np.float64)
-    rc = lib().bps_metric_bank(C.byref(spec), int(seed), None if count_only else _np_ptr(out),
-                               0 if count_only else cap, C.byref(n), C.byref(vol), C.byref(nexp))
-    if count_only and not rc:
-        return out, vol.value, nexp.value
+    rc = lib().bps_metric_bank(C.byref(spec), int(seed), None, 0, C.byref(n), C.byref(vol),
+                               C.byref(nexp))
     if rc:
-        raise BpsError(rc, "bps_metric_bank: %s" % ("bank of %d templates exceeds cap" % n.value
-                                                    if rc == BPS_ERR_CAND_OVERFLOW else
-                                                    "invalid spec"))
+        raise BpsError(rc, "bps_metric_bank: invalid spec" if rc == BPS_ERR_INVALID_ARG else
+                       "bps_metric_bank failed (%d)" % rc)
+    if count_only:
+        return np.zeros((0, 5), np.float64), vol.value, nexp.value
+    if n.value > cap:
+        raise BpsError(BPS_ERR_CAND_OVERFLOW, "bps_metric_bank: bank of %d templates exceeds cap %d"
+                       % (n.value, cap))
+    out = np.zeros((max(1, n.value), 5), np.float64)
+    rc = lib().bps_metric_bank(C.byref(spec), int(seed), _np_ptr(out), out.shape[0], C.byref(n),
+                               C.byref(vol), C.byref(nexp))
+    if rc:
+        raise BpsError(rc, "bps_metric_bank failed (%d)" % rc)
     return out[:n.value].copy(), vol.value, nexp.value
 
 

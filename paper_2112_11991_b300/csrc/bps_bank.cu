@@ -278,10 +278,14 @@ int bps_metric_density(const bps_bank_spec* spec, const bps_template* t, int64_t
                        double* sqrt_det_out)
 {
     if (!spec_ok(spec) || (count > 0 && (!t || !sqrt_det_out)) || count < 0) return BPS_ERR_INVALID_ARG;
-    for (int64_t i = 0; i < count; ++i) {
-        if (!(t[i].porb_s > 0.0) || !(t[i].tau_lts >= 0.0) || !(t[i].ecc >= 0.0 && t[i].ecc < 1.0))
-            return BPS_ERR_INVALID_ARG;
-        sqrt_det_out[i] = density(*spec, t[i]);
+    try {
+        for (int64_t i = 0; i < count; ++i) {
+            if (!(t[i].porb_s > 0.0) || !(t[i].tau_lts >= 0.0) || !(t[i].ecc >= 0.0 && t[i].ecc < 1.0))
+                return BPS_ERR_INVALID_ARG;
+            sqrt_det_out[i] = density(*spec, t[i]);
+        }
+    } catch (...) {
+        return BPS_ERR_OUT_OF_MEMORY;
     }
     return BPS_OK;
 }
@@ -289,16 +293,20 @@ int bps_metric_density(const bps_bank_spec* spec, const bps_template* t, int64_t
 int bps_metric_projected(const bps_bank_spec* spec, const bps_template* t, double* gamma_out)
 {
     if (!spec_ok(spec) || !t || !gamma_out || !(t->porb_s > 0.0)) return BPS_ERR_INVALID_ARG;
-    std::vector<double> gam;
-    projected_metric(*spec, *t, gam);
-    for (size_t i = 0; i < gam.size(); ++i) gamma_out[i] = gam[i];
+    try {
+        std::vector<double> gam;
+        projected_metric(*spec, *t, gam);
+        for (size_t i = 0; i < gam.size(); ++i) gamma_out[i] = gam[i];
+    } catch (...) {
+        return BPS_ERR_OUT_OF_MEMORY;
+    }
     return BPS_OK;
 }
 
-int bps_metric_bank(const bps_bank_spec* spec, uint64_t seed, bps_template* out, int64_t cap,
-                    int64_t* n_out, double* proper_volume, double* n_expected)
+namespace {
+int metric_bank_impl(const bps_bank_spec* spec, uint64_t seed, bps_template* out, int64_t cap,
+                     int64_t* n_out, double* proper_volume, double* n_expected)
 {
-    if (!spec_ok(spec) || !n_out || cap < 0 || (cap > 0 && !out)) return BPS_ERR_INVALID_ARG;
     const bps_bank_spec& sp = *spec;
     const int n = orbital_dims(sp);
     Rng rng(seed);
@@ -345,6 +353,18 @@ int bps_metric_bank(const bps_bank_spec* spec, uint64_t seed, bps_template* out,
         }
     }
     return BPS_OK;
+}
+}  // namespace
+
+int bps_metric_bank(const bps_bank_spec* spec, uint64_t seed, bps_template* out, int64_t cap,
+                    int64_t* n_out, double* proper_volume, double* n_expected)
+{
+    if (!spec_ok(spec) || !n_out || cap < 0 || (cap > 0 && !out)) return BPS_ERR_INVALID_ARG;
+    try {
+        return metric_bank_impl(spec, seed, out, cap, n_out, proper_volume, n_expected);
+    } catch (...) {  // allocation or thread creation failed
+        return BPS_ERR_OUT_OF_MEMORY;
+    }
 }
 
 }  // extern "C"
