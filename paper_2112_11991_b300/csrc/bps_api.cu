@@ -547,7 +547,7 @@ void bps_default_params(bps_search_params* p)
 }
 
 int bps_create(bps_ctx** out, int device)
-{
+try {
     if (!out) return BPS_ERR_INVALID_ARG;
     *out = nullptr;
     int ndev = 0;
@@ -565,6 +565,8 @@ int bps_create(bps_ctx** out, int device)
     }
     *out = ctx;
     return BPS_OK;
+} catch (...) {
+    return BPS_ERR_OUT_OF_MEMORY;  // host allocation failed
 }
 
 static void free_series(Series& s)
@@ -594,7 +596,7 @@ static void free_request(Request& r)
 }
 
 void bps_destroy(bps_ctx* ctx)
-{
+try {
     if (!ctx) return;
     {
         std::lock_guard<std::recursive_mutex> lk(ctx->mu);
@@ -609,13 +611,14 @@ void bps_destroy(bps_ctx* ctx)
         if (ctx->stream) cudaStreamDestroy(ctx->stream);
     }
     delete ctx;
+} catch (...) {
 }
 
 const char* bps_last_error(bps_ctx* ctx) { return ctx ? ctx->err.c_str() : "null context"; }
 
 int bps_load_series(bps_ctx* ctx, const void* data, int64_t n, double tsamp_s, int dtype,
                     int on_device, int64_t* series_id)
-{
+try {
     if (!ctx) return BPS_ERR_INVALID_ARG;
     std::lock_guard<std::recursive_mutex> lk(ctx->mu);
     if (!data || !series_id) return fail(ctx, BPS_ERR_INVALID_ARG, "null pointer");
@@ -662,10 +665,12 @@ int bps_load_series(bps_ctx* ctx, const void* data, int64_t n, double tsamp_s, i
     ctx->series[id] = s;
     *series_id = id;
     return BPS_OK;
+} catch (...) {
+    return BPS_ERR_OUT_OF_MEMORY;  // host allocation failed
 }
 
 int bps_series_update(bps_ctx* ctx, int64_t series_id, const void* data, int on_device)
-{
+try {
     if (!ctx) return BPS_ERR_INVALID_ARG;
     std::lock_guard<std::recursive_mutex> lk(ctx->mu);
     auto it = ctx->series.find(series_id);
@@ -698,10 +703,12 @@ int bps_series_update(bps_ctx* ctx, int64_t series_id, const void* data, int on_
     CK(cudaStreamSynchronize(st));
     s.mean = sum / (double)s.n;
     return BPS_OK;
+} catch (...) {
+    return BPS_ERR_OUT_OF_MEMORY;  // host allocation failed
 }
 
 int bps_load_bank(bps_ctx* ctx, const bps_template* t, int64_t count, int64_t* bank_id)
-{
+try {
     if (!ctx) return BPS_ERR_INVALID_ARG;
     std::lock_guard<std::recursive_mutex> lk(ctx->mu);
     if (!t || !bank_id || count < 1 || count > (1ll << 31))
@@ -723,19 +730,23 @@ int bps_load_bank(bps_ctx* ctx, const bps_template* t, int64_t count, int64_t* b
     ctx->banks[id] = std::move(b);
     *bank_id = id;
     return BPS_OK;
+} catch (...) {
+    return BPS_ERR_OUT_OF_MEMORY;  // host allocation failed
 }
 
 int bps_thresholds(const bps_search_params* params, int64_t n_samples, int64_t n_templates,
                    double* thr_out)
-{
+try {
     if (!params || !thr_out || check_params(nullptr, params, n_samples)) return BPS_ERR_INVALID_ARG;
     thresholds(params, n_samples, n_templates, thr_out);
     return BPS_OK;
+} catch (...) {
+    return BPS_ERR_OUT_OF_MEMORY;  // host allocation failed
 }
 
 int bps_search(bps_ctx* ctx, int64_t series_id, int64_t bank_id, const bps_search_params* params,
                void* cuda_stream, int64_t* req_id)
-{
+try {
     if (!ctx) return BPS_ERR_INVALID_ARG;
     std::lock_guard<std::recursive_mutex> lk(ctx->mu);
     if (!req_id) return fail(ctx, BPS_ERR_INVALID_ARG, "req_id is NULL");
@@ -777,10 +788,12 @@ int bps_search(bps_ctx* ctx, int64_t series_id, int64_t bank_id, const bps_searc
     ctx->reqs[id] = std::move(r);
     *req_id = id;
     return BPS_OK;
+} catch (...) {
+    return BPS_ERR_OUT_OF_MEMORY;  // host allocation failed
 }
 
 int bps_query(bps_ctx* ctx, int64_t req_id, int* done)
-{
+try {
     if (!ctx) return BPS_ERR_INVALID_ARG;
     std::lock_guard<std::recursive_mutex> lk(ctx->mu);
     auto it = ctx->reqs.find(req_id);
@@ -795,11 +808,13 @@ int bps_query(bps_ctx* ctx, int64_t req_id, int* done)
         return BPS_OK;
     }
     return fail(ctx, BPS_ERR_CUDA, "request %lld: %s", (long long)req_id, cudaGetErrorString(e));
+} catch (...) {
+    return BPS_ERR_OUT_OF_MEMORY;  // host allocation failed
 }
 
 int bps_fetch_candidates(bps_ctx* ctx, int64_t req_id, bps_candidate* out, int64_t cap,
                          int64_t* n_written, int64_t* n_total)
-{
+try {
     if (!ctx) return BPS_ERR_INVALID_ARG;
     std::lock_guard<std::recursive_mutex> lk(ctx->mu);
     auto it = ctx->reqs.find(req_id);
@@ -836,10 +851,12 @@ int bps_fetch_candidates(bps_ctx* ctx, int64_t req_id, bps_candidate* out, int64
         return fail(ctx, BPS_ERR_CAND_OVERFLOW, "request %lld found %llu candidates, capacity %lld",
                     (long long)req_id, r.total, (long long)r.cap);
     return BPS_OK;
+} catch (...) {
+    return BPS_ERR_OUT_OF_MEMORY;  // host allocation failed
 }
 
 int bps_unload(bps_ctx* ctx, int64_t id)
-{
+try {
     if (!ctx) return BPS_ERR_INVALID_ARG;
     std::lock_guard<std::recursive_mutex> lk(ctx->mu);
     cudaSetDevice(ctx->device);
@@ -871,18 +888,22 @@ int bps_unload(bps_ctx* ctx, int64_t id)
         return BPS_OK;
     }
     return fail(ctx, BPS_ERR_INVALID_ARG, "unknown id %lld", (long long)id);
+} catch (...) {
+    return BPS_ERR_OUT_OF_MEMORY;  // host allocation failed
 }
 
 int bps_set_profiling(bps_ctx* ctx, int on)
-{
+try {
     if (!ctx) return BPS_ERR_INVALID_ARG;
     std::lock_guard<std::recursive_mutex> lk(ctx->mu);
     ctx->profiling = on != 0;
     return BPS_OK;
+} catch (...) {
+    return BPS_ERR_OUT_OF_MEMORY;  // host allocation failed
 }
 
 int bps_request_stats(bps_ctx* ctx, int64_t req_id, bps_stats* out)
-{
+try {
     if (!ctx) return BPS_ERR_INVALID_ARG;
     std::lock_guard<std::recursive_mutex> lk(ctx->mu);
     auto it = ctx->reqs.find(req_id);
@@ -902,11 +923,13 @@ int bps_request_stats(bps_ctx* ctx, int64_t req_id, bps_stats* out)
         out->stage_ms[e.first] += ms;
     }
     return BPS_OK;
+} catch (...) {
+    return BPS_ERR_OUT_OF_MEMORY;  // host allocation failed
 }
 
 int bps_graph_create(bps_ctx* ctx, int64_t count, const int64_t* series_ids,
                      const int64_t* bank_ids, const bps_search_params* params, int64_t* graph_id)
-{
+try {
     if (!ctx) return BPS_ERR_INVALID_ARG;
     std::lock_guard<std::recursive_mutex> lk(ctx->mu);
     if (count < 1 || !series_ids || !bank_ids || !params || !graph_id)
@@ -979,10 +1002,12 @@ int bps_graph_create(bps_ctx* ctx, int64_t count, const int64_t* series_ids,
     ctx->graphs[id] = g.release();
     *graph_id = id;
     return BPS_OK;
+} catch (...) {
+    return BPS_ERR_OUT_OF_MEMORY;  // host allocation failed
 }
 
 int bps_graph_launch(bps_ctx* ctx, int64_t graph_id, void* cuda_stream)
-{
+try {
     if (!ctx) return BPS_ERR_INVALID_ARG;
     std::lock_guard<std::recursive_mutex> lk(ctx->mu);
     auto it = ctx->graphs.find(graph_id);
@@ -995,11 +1020,13 @@ int bps_graph_launch(bps_ctx* ctx, int64_t graph_id, void* cuda_stream)
     g.launched = true;
     g.fetched = false;
     return BPS_OK;
+} catch (...) {
+    return BPS_ERR_OUT_OF_MEMORY;  // host allocation failed
 }
 
 int bps_graph_fetch(bps_ctx* ctx, int64_t graph_id, int64_t pair, bps_candidate* out, int64_t cap,
                     int64_t* n_written, int64_t* n_total)
-{
+try {
     if (!ctx) return BPS_ERR_INVALID_ARG;
     std::lock_guard<std::recursive_mutex> lk(ctx->mu);
     auto it = ctx->graphs.find(graph_id);
@@ -1041,11 +1068,13 @@ int bps_graph_fetch(bps_ctx* ctx, int64_t graph_id, int64_t pair, bps_candidate*
         return fail(ctx, BPS_ERR_CAND_OVERFLOW, "pair %lld: %llu candidates, capacity %lld",
                     (long long)pair, g.totals[pair], (long long)g.cap);
     return BPS_OK;
+} catch (...) {
+    return BPS_ERR_OUT_OF_MEMORY;  // host allocation failed
 }
 
 int bps_autotune(bps_ctx* ctx, int64_t series_id, int64_t bank_id, const bps_search_params* base,
                  int64_t sample_templates, bps_search_params* best, double* best_ms_per_template)
-{
+try {
     if (!ctx) return BPS_ERR_INVALID_ARG;
     std::lock_guard<std::recursive_mutex> lk(ctx->mu);
     Series* s;
@@ -1108,11 +1137,13 @@ int bps_autotune(bps_ctx* ctx, int64_t series_id, int64_t bank_id, const bps_sea
     *best = bp;
     if (best_ms_per_template) *best_ms_per_template = best_ms / (double)sub.K;
     return BPS_OK;
+} catch (...) {
+    return BPS_ERR_OUT_OF_MEMORY;  // host allocation failed
 }
 
 int bps_index_map(bps_ctx* ctx, int64_t series_id, int64_t bank_id, int64_t template_idx,
                   int32_t* idx_out, int64_t* n_precise)
-{
+try {
     if (!ctx) return BPS_ERR_INVALID_ARG;
     std::lock_guard<std::recursive_mutex> lk(ctx->mu);
     Series* s;
@@ -1146,11 +1177,13 @@ int bps_index_map(bps_ctx* ctx, int64_t series_id, int64_t bank_id, int64_t temp
     CK(cudaStreamSynchronize(st));
     if (n_precise) *n_precise = (int64_t)np;
     return BPS_OK;
+} catch (...) {
+    return BPS_ERR_OUT_OF_MEMORY;  // host allocation failed
 }
 
 int bps_whitened_spectrum(bps_ctx* ctx, int64_t series_id, int64_t bank_id, int64_t t0,
                           int64_t count, const bps_search_params* params, float* pw_out)
-{
+try {
     if (!ctx) return BPS_ERR_INVALID_ARG;
     std::lock_guard<std::recursive_mutex> lk(ctx->mu);
     Series* s;
@@ -1177,11 +1210,13 @@ int bps_whitened_spectrum(bps_ctx* ctx, int64_t series_id, int64_t bank_id, int6
     CK(cudaFreeAsync(w.base, st));
     CK(cudaStreamSynchronize(st));
     return BPS_OK;
+} catch (...) {
+    return BPS_ERR_OUT_OF_MEMORY;  // host allocation failed
 }
 
 int bps_harmonic_sums(bps_ctx* ctx, int64_t series_id, int64_t bank_id, int64_t template_idx,
                       const bps_search_params* params, float* s_out)
-{
+try {
     if (!ctx) return BPS_ERR_INVALID_ARG;
     std::lock_guard<std::recursive_mutex> lk(ctx->mu);
     Series* s;
@@ -1216,6 +1251,8 @@ int bps_harmonic_sums(bps_ctx* ctx, int64_t series_id, int64_t bank_id, int64_t 
     CK(cudaFreeAsync(w.base, st));
     CK(cudaStreamSynchronize(st));
     return BPS_OK;
+} catch (...) {
+    return BPS_ERR_OUT_OF_MEMORY;  // host allocation failed
 }
 
 }  // extern "C"
@@ -1583,7 +1620,7 @@ void worker_main(bps_server* srv)
 extern "C" {
 
 int bps_server_create(bps_ctx* ctx, const bps_server_config* cfg, bps_server** out)
-{
+try {
     if (!ctx || !cfg || !out) return BPS_ERR_INVALID_ARG;
     *out = nullptr;
     if (cfg->max_active < 1 || cfg->max_active > 64 || cfg->groups_in_flight < 1 ||
@@ -1613,10 +1650,12 @@ int bps_server_create(bps_ctx* ctx, const bps_server_config* cfg, bps_server** o
     srv->worker = std::thread(worker_main, srv);
     *out = srv;
     return BPS_OK;
+} catch (...) {
+    return BPS_ERR_OUT_OF_MEMORY;  // host allocation failed
 }
 
 void bps_server_destroy(bps_server* srv)
-{
+try {
     if (!srv) return;
     {
         std::lock_guard<std::mutex> lk(srv->mu);
@@ -1636,6 +1675,7 @@ void bps_server_destroy(bps_server* srv)
         cudaStreamDestroy(s);
     }
     delete srv;
+} catch (...) {
 }
 
 const char* bps_server_last_error(bps_server* srv) { return srv ? srv->err.c_str() : "null server"; }
@@ -1643,7 +1683,7 @@ const char* bps_server_last_error(bps_server* srv) { return srv ? srv->err.c_str
 int bps_server_submit(bps_server* srv, const float* series, int64_t n, double tsamp_s, int dtype,
                       const bps_template* bank, int64_t count, const bps_search_params* params,
                       int64_t* ticket)
-{
+try {
     if (!srv) return BPS_ERR_INVALID_ARG;
     if (!series || !bank || !params || !ticket)
         return sfail(srv, BPS_ERR_INVALID_ARG, "null pointer");
@@ -1703,11 +1743,13 @@ int bps_server_submit(bps_server* srv, const float* series, int64_t n, double ts
     }
     srv->cv.notify_all();
     return BPS_OK;
+} catch (...) {
+    return BPS_ERR_OUT_OF_MEMORY;  // host allocation failed
 }
 
 int bps_server_result(bps_server* srv, int64_t ticket, int32_t timeout_ms, bps_candidate* out,
                       int64_t cap, int64_t* n_written, int64_t* n_total, double* latency_s)
-{
+try {
     if (!srv) return BPS_ERR_INVALID_ARG;
     std::unique_lock<std::mutex> lk(srv->mu);
     auto it = srv->reqs.find(ticket);
@@ -1728,11 +1770,13 @@ int bps_server_result(bps_server* srv, int64_t ticket, int32_t timeout_ms, bps_c
         if (out) srv->reqs.erase(it);
     }
     return rc;
+} catch (...) {
+    return BPS_ERR_OUT_OF_MEMORY;  // host allocation failed
 }
 
 int bps_server_stats(bps_server* srv, int64_t* queued, int64_t* active, int64_t* finished,
                      int64_t* bytes_held)
-{
+try {
     if (!srv) return BPS_ERR_INVALID_ARG;
     std::lock_guard<std::mutex> lk(srv->mu);
     int64_t a = 0, f = 0;
@@ -1745,6 +1789,8 @@ int bps_server_stats(bps_server* srv, int64_t* queued, int64_t* active, int64_t*
     if (finished) *finished = f;
     if (bytes_held) *bytes_held = (int64_t)srv->used;
     return BPS_OK;
+} catch (...) {
+    return BPS_ERR_OUT_OF_MEMORY;  // host allocation failed
 }
 
 }  // extern "C"
@@ -1778,7 +1824,7 @@ double neg_log_q(int n, double x)
 extern "C" int bps_distill(const bps_candidate* in, int64_t n_in, int64_t n_samples,
                            double tsamp_s, double tol_bins, int32_t max_ratio,
                            bps_candidate* out, int64_t cap, int64_t* n_out)
-{
+try {
     if ((!in && n_in > 0) || n_in < 0 || n_samples < 2 || !(tsamp_s > 0.0) ||
         !(tol_bins > 0.0) || max_ratio < 1 || max_ratio > 64 || !n_out || cap < 0)
         return BPS_ERR_INVALID_ARG;
@@ -1826,4 +1872,6 @@ extern "C" int bps_distill(const bps_candidate* in, int64_t n_in, int64_t n_samp
     }
     *n_out = k;
     return k > cap ? BPS_ERR_CAND_OVERFLOW : BPS_OK;
+} catch (...) {
+    return BPS_ERR_OUT_OF_MEMORY;  // host allocation failed
 }

@@ -76,7 +76,7 @@ extern "C" int bps_whitened_spectrum_noalloc(const float* d_series, int64_t n, d
                                              double fill, const bps_template* tmpl,
                                              int32_t whiten_block, float* d_pw_out,
                                              void* cuda_stream)
-{
+try {
     if (!d_series || !tmpl || !d_pw_out) return BPS_ERR_INVALID_ARG;
     const int logn = ilog2_exact(n);
     if (logn < 11) return BPS_ERR_INVALID_ARG;
@@ -150,4 +150,6 @@ extern "C" int bps_whitened_spectrum_noalloc(const float* d_series, int64_t n, d
     if (launch_block_median(P, 1, p, scale, st) != cudaSuccess) return BPS_ERR_CUDA;
     if (launch_whitened(P, scale, 1, p, d_pw_out, st) != cudaSuccess) return BPS_ERR_CUDA;
     return BPS_OK;
+} catch (...) {
+    return BPS_ERR_OUT_OF_MEMORY;  // host allocation failed
 }
