@@ -208,6 +208,13 @@ int bps_set_profiling(bps_ctx* ctx, int on);
  * when profiling was on when the request was enqueued. */
 int bps_request_stats(bps_ctx* ctx, int64_t req_id, bps_stats* out);
 
+/* Failure-path self-test: launches one CTA that polls, with the harmonic sum's bounded
+ * mbarrier wait, a barrier whose phase nothing completes, at most poll_limit times.  The
+ * wait expires, the kernel records it and returns (no fault, nothing in flight), and the
+ * context stays usable.  *timed_out = 1 when the wait expired as designed.  Returns
+ * BPS_OK, or BPS_ERR_INVALID_ARG / BPS_ERR_CUDA. */
+int bps_selftest_bounded_wait(bps_ctx* ctx, int32_t poll_limit, int32_t* timed_out);
+
 /* ---- CUDA graphs: many searches, one launch --------------------------------- */
 
 /* Capture the searches of `count` (series, bank) pairs (series of any supported

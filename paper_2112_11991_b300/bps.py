@@ -41,7 +41,8 @@ EXPORTED = ["bps_default_params", "bps_create", "bps_destroy", "bps_load_series"
             "bps_server_destroy", "bps_server_submit", "bps_server_result", "bps_server_stats",
             "bps_server_last_error", "bps_autotune", "bps_distill", "bps_series_update",
             "bps_graph_create", "bps_graph_launch", "bps_graph_fetch", "bps_default_bank_spec",
-            "bps_metric_density", "bps_metric_projected", "bps_metric_bank"]
+            "bps_metric_density", "bps_metric_projected", "bps_metric_bank",
+            "bps_selftest_bounded_wait"]
 STAGES = ["anchors", "pass1", "pass2", "power", "median", "harmsum"]
 
 
@@ -167,6 +168,8 @@ def lib():
         L.bps_graph_launch.argtypes = [vp, i64, vp]
         L.bps_graph_fetch.restype = i32
         L.bps_graph_fetch.argtypes = [vp, i64, i64, vp, i64, P(i64), P(i64)]
+        L.bps_selftest_bounded_wait.restype = i32
+        L.bps_selftest_bounded_wait.argtypes = [vp, i32, P(i32)]
         L.bps_default_bank_spec.restype = None
         L.bps_default_bank_spec.argtypes = [P(bps_bank_spec)]
         L.bps_metric_density.restype = i32
@@ -441,6 +444,13 @@ class Context:
             self._check(rc, "bps_graph_fetch")
         return out[:nw.value], nt.value
 
+    def selftest_bounded_wait(self, poll_limit: int = 1000) -> bool:
+        """Run the bounded-wait self-test kernel; True when its wait expired as designed."""
+        t = C.c_int32()
+        self._check(lib().bps_selftest_bounded_wait(self.h, int(poll_limit), C.byref(t)),
+                    "bps_selftest_bounded_wait")
+        return bool(t.value)
+
     def set_profiling(self, on: bool):
         self._check(lib().bps_set_profiling(self.h, int(bool(on))), "bps_set_profiling")
 
@@ -637,6 +647,10 @@ def bps_distill(cin, n_in, n_samples, tsamp, tol, max_ratio, out, cap, n_out):
 
 def bps_set_profiling(ctx, on):
     return lib().bps_set_profiling(ctx, on)
+
+
+def bps_selftest_bounded_wait(ctx, limit, timed_out):
+    return lib().bps_selftest_bounded_wait(ctx, limit, timed_out)
 
 
 def bps_default_bank_spec(spec):

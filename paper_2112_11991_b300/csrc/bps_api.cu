@@ -927,6 +927,27 @@ try {
     return BPS_ERR_OUT_OF_MEMORY;  // host allocation failed
 }
 
+int bps_selftest_bounded_wait(bps_ctx* ctx, int32_t poll_limit, int32_t* timed_out)
+try {
+    if (!ctx) return BPS_ERR_INVALID_ARG;
+    std::lock_guard<std::recursive_mutex> lk(ctx->mu);
+    if (poll_limit < 1 || !timed_out) return fail(ctx, BPS_ERR_INVALID_ARG, "bad self-test arguments");
+    CK(cudaSetDevice(ctx->device));
+    unsigned long long* d = nullptr;
+    unsigned long long h = 0;
+    CK(cudaMalloc((void**)&d, sizeof(unsigned long long)));
+    cudaError_t e = cudaMemsetAsync(d, 0, sizeof(unsigned long long), ctx->stream);
+    if (e == cudaSuccess) e = launch_wait_selftest(poll_limit, d, ctx->stream);
+    if (e == cudaSuccess) e = cudaMemcpyAsync(&h, d, sizeof(h), cudaMemcpyDeviceToHost, ctx->stream);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(ctx->stream);
+    cudaFree(d);
+    if (e != cudaSuccess) return fail(ctx, BPS_ERR_CUDA, "wait self-test: %s", cudaGetErrorString(e));
+    *timed_out = h == 1ull ? 1 : 0;
+    return BPS_OK;
+} catch (...) {
+    return BPS_ERR_OUT_OF_MEMORY;  // host allocation failed
+}
+
 int bps_graph_create(bps_ctx* ctx, int64_t count, const int64_t* series_ids,
                      const int64_t* bank_ids, const bps_search_params* params, int64_t* graph_id)
 try {

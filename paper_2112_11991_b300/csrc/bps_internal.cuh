@@ -131,6 +131,9 @@ cudaError_t set_smem_attributes();
 // Function attributes and occupancy of the median and harmonic-sum kernels, once per
 // device (host-side only; called before a graph capture so none happens during one).
 cudaError_t prepare_detect_kernels();
+// One CTA polls an mbarrier that never completes at most `limit` times; status[0] = 1
+// when the wait expired (the bounded-wait path of the harmonic sum, exercised safely).
+cudaError_t launch_wait_selftest(int limit, unsigned long long* status, cudaStream_t s);
 cudaError_t launch_pass1(const SeriesView& x, const Anchor* anc, int nt, const Plan& p,
                          const float2* tw, float2* Y, cudaStream_t s);
 cudaError_t launch_pass2(const float2* Y, int nt, const Plan& p, const float2* tw,

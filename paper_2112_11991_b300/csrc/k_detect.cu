@@ -275,12 +275,25 @@ __device__ __forceinline__ bool mbar_try_wait(uint64_t* bar, uint32_t phase)
 
 constexpr int kWaitLimit = 1 << 22;
 
-// Bounded wait for the given phase parity of an mbarrier; false after the limit.
-__device__ __forceinline__ bool mbar_wait_parity(uint64_t* bar, uint32_t parity)
+// Bounded wait for the given phase parity of an mbarrier; false after `limit` polls.
+__device__ __forceinline__ bool mbar_wait_parity(uint64_t* bar, uint32_t parity, int limit = kWaitLimit)
 {
-    for (int it = 0; it < kWaitLimit; ++it)
+    for (int it = 0; it < limit; ++it)
         if (mbar_try_wait(bar, parity)) return true;
     return false;
+}
+
+// Self-test of the bounded waits: an mbarrier expecting one arrival that nothing makes,
+// so its phase never completes; thread 0 polls it at most `limit` times with the same
+// helper the harmonic sum uses and records the outcome (1 = the wait expired).  No copy
+// is in flight and nothing faults: the kernel simply returns.
+__global__ void k_wait_selftest(int limit, unsigned long long* status)
+{
+    __shared__ __align__(8) uint64_t bar;
+    if (threadIdx.x == 0) {
+        mbar_init(&bar, 1);
+        status[0] = mbar_wait_parity(&bar, 0u, limit) ? 0ull : 1ull;
+    }
 }
 
 // Arrive on an mbarrier (release; one arrival).
@@ -602,6 +615,13 @@ cudaError_t launch_harmsum(const float* P, const float* scale, int nt, int64_t t
         case 16: return launch_hs<16>(P, nt, tidx0, p, thr, cands, cap, count, s_out, s);
         default: return cudaErrorInvalidValue;
     }
+}
+
+cudaError_t launch_wait_selftest(int limit, unsigned long long* status, cudaStream_t s)
+{
+    if (limit < 1) return cudaErrorInvalidValue;
+    k_wait_selftest<<<1, 32, 0, s>>>(limit, status);
+    return cudaGetLastError();
 }
 
 cudaError_t prepare_detect_kernels()

@@ -315,3 +315,20 @@ def test_pass1_tiles_identical(bps, ctx, logn):
     assert np.array_equal(res[13][1], res[14][1]) and res[13][1].size > 0
     ctx.unload(sid)
     ctx.unload(bid)
+
+
+def test_bounded_wait_expires_and_context_survives(bps, ctx, w1):
+    """A kernel polling an mbarrier whose phase nothing completes gives up after its
+    limit and reports it; the context keeps working (a search right after matches one
+    before)."""
+    n = 1 << 16
+    sid = ctx.load_series(w1.series[:n].copy(), w1.tsamp)
+    bid = ctx.load_bank(w1.bank[:2])
+    before, _ = ctx.fetch_candidates(ctx.search(sid, bid, bps.default_params(sigma_thr=4.0)))
+    assert ctx.selftest_bounded_wait(1000) is True
+    after, _ = ctx.fetch_candidates(ctx.search(sid, bid, bps.default_params(sigma_thr=4.0)))
+    assert np.array_equal(before, after)
+    with pytest.raises(bps.BpsError):
+        ctx.selftest_bounded_wait(0)
+    ctx.unload(sid)
+    ctx.unload(bid)
