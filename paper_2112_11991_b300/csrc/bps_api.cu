@@ -267,6 +267,17 @@ struct Workspace {
 
 size_t align256(size_t v) { return (v + 255) & ~(size_t)255; }
 
+// Fetch order of candidates: (template_idx, nharm, bin), deterministic whatever the order
+// in which the device appended them.
+void sort_candidates(std::vector<bps_candidate>& c)
+{
+    std::sort(c.begin(), c.end(), [](const bps_candidate& a, const bps_candidate& b) {
+        if (a.template_idx != b.template_idx) return a.template_idx < b.template_idx;
+        if (a.nharm != b.nharm) return a.nharm < b.nharm;
+        return a.bin < b.bin;
+    });
+}
+
 // Anchors are computed for a chunk of up to kAnchorChunk batches in one launch.
 constexpr int kAnchorChunk = 8;
 
@@ -831,11 +842,7 @@ try {
         r.result.resize((size_t)kept);
         static_assert(sizeof(Cand) == sizeof(bps_candidate), "candidate layout");
         if (kept) CK(cudaMemcpy(r.result.data(), r.d_cands, sizeof(Cand) * kept, cudaMemcpyDeviceToHost));
-        std::sort(r.result.begin(), r.result.end(), [](const bps_candidate& a, const bps_candidate& b) {
-            if (a.template_idx != b.template_idx) return a.template_idx < b.template_idx;
-            if (a.nharm != b.nharm) return a.nharm < b.nharm;
-            return a.bin < b.bin;
-        });
+        sort_candidates(r.result);
         r.synced = true;
         cudaFree(r.d_cands);
         r.d_cands = nullptr;
@@ -1071,11 +1078,7 @@ try {
             if (kept)
                 CK(cudaMemcpy(g.results[i].data(), g.cands + (size_t)i * g.cap, sizeof(Cand) * kept,
                               cudaMemcpyDeviceToHost));
-            std::sort(g.results[i].begin(), g.results[i].end(), [](const bps_candidate& a, const bps_candidate& b) {
-                if (a.template_idx != b.template_idx) return a.template_idx < b.template_idx;
-                if (a.nharm != b.nharm) return a.nharm < b.nharm;
-                return a.bin < b.bin;
-            });
+            sort_candidates(g.results[i]);
         }
         g.fetched = true;
     }
@@ -1565,11 +1568,7 @@ bool advance(bps_server* srv, SReq& q)
             const int64_t kept = (int64_t)q.result.size();
             if (kept > 0 && kept <= kPinnedCands)
                 std::memcpy(q.result.data(), q.h_cands, sizeof(Cand) * kept);
-            std::sort(q.result.begin(), q.result.end(), [](const bps_candidate& a, const bps_candidate& b) {
-                if (a.template_idx != b.template_idx) return a.template_idx < b.template_idx;
-                if (a.nharm != b.nharm) return a.nharm < b.nharm;
-                return a.bin < b.bin;
-            });
+            sort_candidates(q.result);
             if (q.status & 1ull) {
                 q.rc = BPS_ERR_TIMEOUT;
                 q.err = "a bounded device wait expired; results incomplete";
