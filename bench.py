@@ -338,7 +338,7 @@ def run_uneven(bps, ctx, steps=2, warmup=1, seed=11):
     tuned = {}
     for logn, (sid, bid) in sorted(n_of.items()):
         best, _ = ctx.autotune(sid, bid, prm, sample_templates=64)
-        tuned[logn] = [best.log_tile, best.log_tile2, best.batch]
+        tuned[logn] = [best.log_tile, best.log_tile2, best.batch, best.log_cols]
     gid = ctx.graph_create(pairs, prm)
     st = torch.cuda.Stream()
     ms = []
@@ -406,7 +406,7 @@ def run_elliptical_f16(bps, ctx, steps=2, warmup=1):
                         "tau U[0,20] lt-s, e U[0,0.1]), FP16 series + scale per 4096, FP32 FFT" % K,
             "value": K / (statistics.mean(ms) / 1e3), "unit": UNIT,
             "ms_per_step": statistics.mean(ms), "steps": steps, "warmup": warmup,
-            "autotuned": [best.log_tile, best.log_tile2, best.batch],
+            "autotuned": [best.log_tile, best.log_tile2, best.batch, best.log_cols],
             "candidates": int(total),
             "pw_max_rel_diff_vs_fp32_storage": err}
 
@@ -454,6 +454,7 @@ def main():
         best, ms_t = ctx.autotune(sid, bid, bps.default_params(cand_cap=CAND_CAP),
                                   sample_templates=min(64, K))
         tuned = {"log_tile": best.log_tile, "log_tile2": best.log_tile2, "batch": best.batch,
+                 "log_cols": best.log_cols,
                  "ms_per_template_sample": ms_t}
 
     def timed_steps(mode, steps, warmup, profile):

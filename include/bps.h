@@ -93,6 +93,10 @@ typedef struct {
     int32_t log_tile;      /* FFT pass-1 tile: 2^log_tile complex values per CTA,    */
                            /* 13 or 14; 0 = library's choice (14)                     */
     int32_t log_tile2;     /* FFT pass-2 tile, 13 or 14; 0 = library's choice (13)   */
+    int32_t log_cols;      /* log2 C of the four-step split N/2 = R x C (pass-1 column  */
+                           /* length R, pass-2 row length C: the radix structure of   */
+                           /* both passes), in [max(5, log2(N/2) - 12),               */
+                           /* min(log2(N/2) - 5, 12)]; 0 = library's choice           */
 } bps_search_params;
 
 typedef struct bps_ctx bps_ctx;
@@ -302,7 +306,8 @@ int bps_distill(const bps_candidate* in, int64_t n_in, int64_t n_samples, double
  * fastest parameters to *best (other fields copied from *base) and its device time per
  * template to *best_ms_per_template, and remembers the choice in the context: later
  * searches of the same series length, mode and harmonic count that leave log_tile,
- * log_tile2 or batch at 0 use it. */
+ * log_tile2, log_cols or batch at 0 use it.  Candidates: pass-1 and pass-2 tiles 13/14,
+ * the library's four-step split and its neighbours log_cols +- 1, batches 8..64. */
 int bps_autotune(bps_ctx* ctx, int64_t series_id, int64_t bank_id, const bps_search_params* base,
                  int64_t sample_templates, bps_search_params* best, double* best_ms_per_template);
 

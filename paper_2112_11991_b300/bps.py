@@ -74,7 +74,7 @@ class bps_search_params(C.Structure):
     _fields_ = [("nharm_max", C.c_int32), ("whiten_block", C.c_int32), ("sigma_thr", C.c_double),
                 ("auto_thr", C.c_int32), ("mode", C.c_int32), ("cand_cap", C.c_int64),
                 ("precision", C.c_int32), ("batch", C.c_int32), ("log_tile", C.c_int32),
-                ("log_tile2", C.c_int32)]
+                ("log_tile2", C.c_int32), ("log_cols", C.c_int32)]
 
 
 class bps_server_config(C.Structure):

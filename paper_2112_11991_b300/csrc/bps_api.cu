@@ -80,8 +80,8 @@ struct bps_ctx {
     std::map<FftKey, cufftHandle> ffts;
     float2* tw = nullptr;
     bool profiling = false;
-    // autotuned launch shapes per (log2 n, mode, log2 nharm): tile1, tile2, batch
-    std::map<int, std::array<int, 3>> tuned;
+    // autotuned launch shapes per (log2 n, mode, log2 nharm): tile1, tile2, batch, log C
+    std::map<int, std::array<int, 4>> tuned;
     std::map<int64_t, GraphObj*> graphs;
 };
 
@@ -170,6 +170,9 @@ int check_params(bps_ctx* ctx, const bps_search_params* pr, int64_t n)
     if ((pr->log_tile != 0 && pr->log_tile != 13 && pr->log_tile != 14) ||
         (pr->log_tile2 != 0 && pr->log_tile2 != 13 && pr->log_tile2 != 14))
         return fail(ctx, BPS_ERR_INVALID_ARG, "log_tile and log_tile2 must be 0, 13 or 14");
+    if (pr->log_cols != 0 && !log_cols_ok(ilog2(n) - 1, pr->log_cols))
+        return fail(ctx, BPS_ERR_INVALID_ARG, "log_cols %d is not a valid split of %lld samples",
+                    pr->log_cols, (long long)n);
     return BPS_OK;
 }
 
@@ -197,15 +200,17 @@ int make_plan(bps_ctx* ctx, const Series& s, const Bank& b, const bps_search_par
     p.logn = ilog2(s.n);
     p.M = s.n / 2;
     p.logM = p.logn - 1;
-    int t1 = 14, t2 = 13;
+    int t1 = 14, t2 = 13, lc = 0;
     if (ctx) {
         auto it = ctx->tuned.find(tune_key(ilog2(s.n), pr.mode, ilog2(pr.nharm_max)));
         if (it != ctx->tuned.end()) {
             t1 = it->second[0];
             t2 = it->second[1];
+            lc = it->second[3];
         }
     }
-    plan_geometry(p, pr.log_tile ? pr.log_tile : t1, pr.log_tile2 ? pr.log_tile2 : t2);
+    plan_geometry(p, pr.log_tile ? pr.log_tile : t1, pr.log_tile2 ? pr.log_tile2 : t2,
+                  pr.log_cols ? pr.log_cols : lc);
     p.logW = ilog2(pr.whiten_block);
     // transposed power when a whitening block lies within one k2 (W <= R) and the warp
     // median applies (W <= 1024): pass 2 then writes whole rows
@@ -555,6 +560,7 @@ void bps_default_params(bps_search_params* p)
     p->cand_cap = 1 << 20;
     p->precision = 0;
     p->batch = 0;
+    p->log_cols = 0;
 }
 
 int bps_create(bps_ctx** out, int device)
@@ -1121,8 +1127,17 @@ try {
     cudaEventCreate(&e1);
     const int tiles[2] = {13, 14};
     const int batches[4] = {8, 16, 32, 64};
+    // four-step splits: the caller's, else the library's and its valid neighbours
+    const int logM = ilog2(s->n) - 1;
+    std::vector<int> splits;
+    if (base->log_cols) splits.push_back(base->log_cols);
+    else if (base->mode == BPS_MODE_PLAIN) splits.push_back(0);
+    else
+        for (int d : {0, -1, 1})
+            if (log_cols_ok(logM, default_log_cols(logM) + d)) splits.push_back(default_log_cols(logM) + d);
     double best_ms = 1e30;
     bps_search_params bp = *base;
+    for (int lc : splits)
     for (int t1 : tiles)
         for (int t2 : tiles)
             for (int nb : batches) {
@@ -1130,6 +1145,7 @@ try {
                 bps_search_params pr = *base;
                 pr.log_tile = t1;
                 pr.log_tile2 = t2;
+                pr.log_cols = lc;
                 pr.batch = nb;
                 double ms_best = 1e30;
                 for (int rep = 0; rep < 2 && !rc; ++rep) {
@@ -1157,7 +1173,7 @@ try {
     cudaFree(cnt);
     if (rc) return rc;
     ctx->tuned[tune_key(ilog2(s->n), base->mode, ilog2(base->nharm_max))] = {bp.log_tile, bp.log_tile2,
-                                                                          bp.batch};
+                                                                          bp.batch, bp.log_cols};
     *best = bp;
     if (best_ms_per_template) *best_ms_per_template = best_ms / (double)sub.K;
     return BPS_OK;

@@ -59,18 +59,29 @@ struct Plan {
 // Four-step split of the packed FFT, M = R * C, with CTA tiles of 2^logTile (pass 1)
 // and 2^logTile2 (pass 2) complex values in shared memory (13: 256 threads, two CTAs
 // per SM; 14: 512 threads, one): C = 2^min(10, logM - 5) row length (pass 2), raised
-// to M / 2^12 where R would exceed 2^12 column length (pass 1); G = tile1 / R adjacent
-// columns per pass-1 CTA, NP = tile2 / (2C) row pairs per pass-2 CTA.
-inline void plan_geometry(Plan& p, int logTile = 14, int logTile2 = 13)
+// to M / 2^12 where R would exceed 2^12 column length (pass 1), unless logCols (checked
+// by log_cols_ok) chooses another split; G = tile1 / R adjacent columns per pass-1 CTA,
+// NP = tile2 / (2C) row pairs per pass-2 CTA.
+inline int default_log_cols(int logM)
+{
+    int lc = logM - 5 < 10 ? logM - 5 : 10;
+    if (logM - lc > 12) lc = logM - 12;
+    return lc;
+}
+
+// Valid four-step splits: C >= 32, R >= 32, R <= 2^12, C <= 2^12 (pass 2's split
+// twiddles W_{2C}^k come from the 8192-entry table).
+inline bool log_cols_ok(int logM, int lc)
+{
+    return lc >= 5 && lc >= logM - 12 && lc <= logM - 5 && lc <= 12;
+}
+
+inline void plan_geometry(Plan& p, int logTile = 14, int logTile2 = 13, int logCols = 0)
 {
     p.logTile = logTile;
     p.logTile2 = logTile2;
-    p.logC = p.logM - 5 < 10 ? p.logM - 5 : 10;
+    p.logC = logCols ? logCols : default_log_cols(p.logM);
     p.logR = p.logM - p.logC;
-    if (p.logR > 12) {
-        p.logR = 12;
-        p.logC = p.logM - 12;
-    }
     const int lt = logTile > p.logR ? logTile : p.logR;  // a column must fit one tile
     p.logG = p.logC < lt - p.logR ? p.logC : lt - p.logR;
     p.logNP = (logTile2 - 1 - p.logC) < (p.logR - 1) ? (logTile2 - 1 - p.logC) : (p.logR - 1);

@@ -288,6 +288,7 @@ def test_autotune_choice_and_invariance(bps, ctx, w1):
                                                                         batch=8)))
     best, ms = ctx.autotune(sid, bid, bps.default_params(), sample_templates=8)
     assert best.log_tile in (13, 14) and best.log_tile2 in (13, 14) and best.batch in (4, 8)
+    assert best.log_cols in (9, 10, 11)  # 2^18 samples: the default split (10) or a neighbour
     assert ms > 0
     got, _ = ctx.fetch_candidates(ctx.search(sid, bid, bps.default_params()))  # uses the choice
     assert np.array_equal(got, ref)
@@ -330,5 +331,32 @@ def test_bounded_wait_expires_and_context_survives(bps, ctx, w1):
     assert np.array_equal(before, after)
     with pytest.raises(bps.BpsError):
         ctx.selftest_bounded_wait(0)
+    ctx.unload(sid)
+    ctx.unload(bid)
+
+
+@pytest.mark.parametrize("logn,log_cols,W", [(16, 9, 1024), (18, 9, 1024), (18, 11, 1024),
+                                             (20, 11, 1024), (20, 12, 1024), (21, 12, 256)])
+def test_four_step_splits_against_oracle(bps, ctx, orc, logn, log_cols, W):
+    """Other four-step splits N/2 = R x C (other radix structures of both FFT passes;
+    with C = 4096 and W <= R the row-major power layout and the transposing median)
+    give the oracle's whitened power and candidates."""
+    n, ts = 1 << logn, 64e-6
+    T = n * ts
+    p = synth.Pulsar(period_s=0.023, porb_s=6 * T, tau_lts=0.06, phi_rad=0.9, amp=0.4)
+    x = synth.inject(synth.noise(n, 3000 + logn), ts, p)
+    bank = np.array([p.orbit(), (8 * T, 0.03, 2.0, 0.0, 0.0)])
+    sid = ctx.load_series(x, ts)
+    bid = ctx.load_bank(bank)
+    prm = bps.default_params(log_cols=log_cols, sigma_thr=5.0, whiten_block=W)
+    pw = ctx.whitened_spectrum(sid, bid, 0, 2, n, prm)
+    gc, _ = ctx.fetch_candidates(ctx.search(sid, bid, prm))
+    oc, res = oracle_on_gpu_maps(ctx, orc, sid, bid, x, ts, bank, want_arrays=True, sigma=5.0,
+                                 whiten_block=W)
+    for t in range(2):
+        assert pw_close(pw[t], res[t]["Pw"]) <= PW_TOL, t
+    compare_candidates(gc, oc, bps.thresholds(prm, n, 2))
+    with pytest.raises(bps.BpsError):
+        ctx.search(sid, bid, bps.default_params(log_cols=logn))  # R < 32
     ctx.unload(sid)
     ctx.unload(bid)
