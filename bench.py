@@ -54,6 +54,8 @@ def parse():
     ap.add_argument("--batch", type=int, default=0)
     ap.add_argument("--log-tile", type=int, default=0)
     ap.add_argument("--log-tile2", type=int, default=0)
+    ap.add_argument("--log-cols", type=int, default=0,
+                    help="log2 of the four-step row length C (0 = library / autotuner)")
     ap.add_argument("--dtype", default="f32", choices=["f32", "f16"],
                     help="series storage on the device: f32, or f16 with a power-of-two "
                          "scale per 4096 samples (FFT arithmetic is FP32 either way)")
@@ -94,15 +96,23 @@ def kernel_source_hash():
     return h.hexdigest()[:16]
 
 
-def ncu_traffic(stage, workload, templates_per_launch):
-    """DRAM bytes per launch of `stage` from the committed ncu summary, scaled from the
-    captured launch's templates to this run's (the traffic of these kernels grows in
-    proportion to the templates a launch processes), or None when absent or taken on
-    different kernel sources."""
+def geometry_key(logn, log_cols, log_tile, log_tile2):
+    """Traffic key of a launch shape: four-step split and the two pass tiles (0 = the
+    library's defaults: C = 2^min(10, log M - 5) raised to M / 2^12, tiles 14 / 13)."""
+    logM = logn - 1
+    lc = log_cols or (min(10, logM - 5) if logM - min(10, logM - 5) <= 12 else logM - 12)
+    return "c%d_t%d_%d" % (lc, log_tile or 14, log_tile2 or 13)
+
+
+def ncu_traffic(stage, workload, templates_per_launch, geom):
+    """DRAM bytes per launch of `stage` from the committed ncu summary for this launch
+    shape, scaled from the captured launch's templates to this run's (the traffic of
+    these kernels grows in proportion to the templates a launch processes), or None when
+    absent, captured on another shape or on different kernel sources."""
     try:
         with open(os.path.join(ROOT, "profiles", "traffic.json")) as f:
             d = json.load(f)
-        e = d[workload][stage]
+        e = d[workload][geom][stage]
         if e.get("source_hash") != kernel_source_hash():
             return None
         return float(e["dram_bytes_per_launch"]) * templates_per_launch / float(e["templates_per_launch"])
@@ -450,7 +460,7 @@ def main():
 
     # launch shapes of the fused form chosen by the library's autotuner on 64 templates
     tuned = None
-    if args.batch == 0 and args.log_tile == 0 and args.log_tile2 == 0:
+    if args.batch == 0 and args.log_tile == 0 and args.log_tile2 == 0 and args.log_cols == 0:
         best, ms_t = ctx.autotune(sid, bid, bps.default_params(cand_cap=CAND_CAP),
                                   sample_templates=min(64, K))
         tuned = {"log_tile": best.log_tile, "log_tile2": best.log_tile2, "batch": best.batch,
@@ -460,7 +470,8 @@ def main():
     def timed_steps(mode, steps, warmup, profile):
         prm = bps.default_params(mode=mode, batch=args.batch if mode == 0 else 0,
                                  cand_cap=CAND_CAP, log_tile=args.log_tile,
-                                 log_tile2=args.log_tile2)
+                                 log_tile2=args.log_tile2,
+                                 log_cols=args.log_cols if mode == 0 else 0)
         ctx.set_profiling(False)
         for _ in range(warmup):
             rid = ctx.search(sid, bid, prm, stream=stream)
@@ -511,7 +522,7 @@ def main():
     e2e_ms = []
     d2h = 0
     prm = bps.default_params(batch=args.batch, cand_cap=CAND_CAP, log_tile=args.log_tile,
-                                 log_tile2=args.log_tile2)
+                             log_tile2=args.log_tile2, log_cols=args.log_cols)
     for i in range(args.warmup + args.steps):
         torch.cuda.synchronize(dev)
         t0 = time.perf_counter()
@@ -542,9 +553,14 @@ def main():
     per_launch_ms = stage_ms[dom] / max(1, stage_launch[dom])
     alg_bytes = STAGE_BYTES_PER_N[dom] * n * batch
     achieved = alg_bytes / (per_launch_ms * 1e-3) / 1e9
-    traffic = ncu_traffic(dom, "htru_2p%d" % args.logn, batch)
+    if tuned:
+        geom = geometry_key(args.logn, tuned["log_cols"], tuned["log_tile"], tuned["log_tile2"])
+    else:
+        geom = geometry_key(args.logn, args.log_cols, args.log_tile, args.log_tile2)
+    traffic = ncu_traffic(dom, "htru_2p%d" % args.logn, batch, geom)
     roof = {"bound": "hbm", "kernel": dom, "achieved": achieved, "peak": peak, "unit": "GB/s",
             "frac": achieved / peak, "peak_kind": peak_kind, "traffic": traffic,
+            "launch_shape": geom,
             "alg_bytes_per_launch": alg_bytes, "templates_per_launch": batch,
             "ms_per_launch": per_launch_ms}
     path_gbs = PATH_BYTES_PER_N * n * K * args.steps / (sum(ms) / 1e3) / 1e9
