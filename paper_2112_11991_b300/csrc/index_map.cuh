@@ -113,21 +113,34 @@ __device__ __forceinline__ float gather_sample(const SeriesView& x, int n, int i
     return __half2float(h) * __ldg(x.scale + (idx >> 12));
 }
 
-// Two gathered samples x[i0], x[i1] whose indices are at most a few samples apart:
-// for FP16 storage one scale load serves both unless they straddle a 4096-sample block.
-__device__ __forceinline__ float2 gather_pair(const SeriesView& x, int n, int i0, int i1)
+// Two gathered FP32 samples x[i0], x[i1] (the series mean outside [0, n)).
+__device__ __forceinline__ float2 gather_pair_f32(const SeriesView& x, int n, int i0, int i1)
 {
-    if (x.f32) {
-        return make_float2((unsigned)i0 < (unsigned)n ? __ldg(x.f32 + i0) : x.fill,
-                           (unsigned)i1 < (unsigned)n ? __ldg(x.f32 + i1) : x.fill);
+    return make_float2((unsigned)i0 < (unsigned)n ? __ldg(x.f32 + i0) : x.fill,
+                       (unsigned)i1 < (unsigned)n ? __ldg(x.f32 + i1) : x.fill);
+}
+
+// The 32 FP16 samples of a first-stage butterfly (pairs id[2s], id[2s+1] -> v[s]): every
+// load first (the halves and their block scales), then the conversions, so all the
+// loads are in flight together (converting each value as it arrives serialised them).
+__device__ __forceinline__ void gather_f16_butterfly(const SeriesView& x, int n, const int (&id)[32],
+                                                     float2 (&v)[16])
+{
+    unsigned short hv[32];
+    float sv[32];
+#pragma unroll
+    for (int q = 0; q < 32; ++q) {
+        const int i = id[q];
+        const bool in = (unsigned)i < (unsigned)n;
+        hv[q] = in ? __ldg(x.f16 + i) : (unsigned short)0;
+        sv[q] = in ? __ldg(x.scale + (i >> 12)) : 0.f;
     }
-    const bool in0 = (unsigned)i0 < (unsigned)n, in1 = (unsigned)i1 < (unsigned)n;
-    const int c0 = in0 ? i0 : (in1 ? i1 : 0);
-    const float s0 = __ldg(x.scale + (c0 >> 12));
-    const float s1 = ((i1 >> 12) == (c0 >> 12)) ? s0 : __ldg(x.scale + ((in1 ? i1 : c0) >> 12));
-    const float v0 = in0 ? __half2float(__ushort_as_half(__ldg(x.f16 + i0))) * s0 : x.fill;
-    const float v1 = in1 ? __half2float(__ushort_as_half(__ldg(x.f16 + i1))) * s1 : x.fill;
-    return make_float2(v0, v1);
+#pragma unroll
+    for (int s = 0; s < 16; ++s) {
+        const bool in0 = (unsigned)id[2 * s] < (unsigned)n, in1 = (unsigned)id[2 * s + 1] < (unsigned)n;
+        v[s] = make_float2(in0 ? __half2float(__ushort_as_half(hv[2 * s])) * sv[2 * s] : x.fill,
+                           in1 ? __half2float(__ushort_as_half(hv[2 * s + 1])) * sv[2 * s + 1] : x.fill);
+    }
 }
 
 }  // namespace bps

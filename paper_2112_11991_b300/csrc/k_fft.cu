@@ -359,9 +359,12 @@ __global__ void __launch_bounds__(512, 1) k_pass1(SeriesView x, const Anchor* __
         int id[32];
         pass1_indices(at, p.logB, logQ, logC, c0 + g, j, id);
         float2 v[16];
+        if (x.f32) {
 #pragma unroll
-        for (int s = 0; s < 16; ++s)
-            v[s] = gather_pair(x, n, id[2 * s], id[2 * s + 1]);
+            for (int s = 0; s < 16; ++s) v[s] = gather_pair_f32(x, n, id[2 * s], id[2 * s + 1]);
+        } else {
+            gather_f16_butterfly(x, n, id, v);
+        }
         Radix<4>::dft(v);
 #pragma unroll
         for (int s = 0; s < 16; ++s) sm[pad(g + G * (16 * j + s))] = v[Radix<4>::out_pos(s)];
