@@ -247,6 +247,8 @@ SeriesView view_of(const Series& s)
     v.f32 = s.dtype == BPS_F32 ? s.f32 : nullptr;
     v.f16 = s.dtype == BPS_F16_SCALED ? s.f16 : nullptr;
     v.scale = s.scale;
+    v.uscalep = s.scale ? s.scale + ((s.n + 4095) >> 12) : nullptr;
+    v.uscale = 0.f;
     v.fill = (float)s.mean;
     v.fillp = s.d_fill;
     return v;
@@ -672,7 +674,7 @@ try {
         s.owned = tmp;
     } else {
         CK(cudaMalloc((void**)&s.f16, sizeof(uint16_t) * n));
-        CK(cudaMalloc((void**)&s.scale, sizeof(float) * ((n + 4095) >> 12)));
+        CK(cudaMalloc((void**)&s.scale, sizeof(float) * (((n + 4095) >> 12) + 1)));
         CK(launch_f16_pack(src, n, s.f16, s.scale, st));
     }
     CK(cudaStreamSynchronize(st));
@@ -1469,7 +1471,7 @@ bool admit_one(bps_server* srv, SReq& q, int slot)
     } else {
         chk(cudaMallocAsync((void**)&q.d_stage, 4 * n, st));
         chk(cudaMallocAsync((void**)&q.s.f16, 2 * n, st));
-        chk(cudaMallocAsync((void**)&q.s.scale, 4 * ((n + 4095) >> 12), st));
+        chk(cudaMallocAsync((void**)&q.s.scale, 4 * (((n + 4095) >> 12) + 1), st));
         src = q.d_stage;
     }
     chk(cudaMallocAsync((void**)&q.d_sum, sizeof(double), st));

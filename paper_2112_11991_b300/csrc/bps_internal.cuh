@@ -123,9 +123,12 @@ struct Cand {
 struct SeriesView {
     const float* f32;          // FP32 samples (or nullptr)
     const uint16_t* f16;       // FP16 samples (or nullptr)
-    const float* scale;        // per-4096-sample scale for FP16
+    const float* scale;        // per-4096-sample scale for FP16; scale[n_blocks] holds the
+                               // common scale when all blocks share one, else 0
     float fill;                // mean of the series (value for out-of-range samples)
     const float* fillp;        // device copy of the fill value (used when non-null)
+    const float* uscalep;      // &scale[n_blocks] (FP16; nullptr otherwise)
+    float uscale;              // *uscalep, read at kernel entry (0: per-block scales)
 };
 
 // Launchers (stream-ordered, return cudaGetLastError()).
@@ -168,6 +171,8 @@ cudaError_t launch_harmsum(const float* P, const float* scale, int nt, int64_t t
 cudaError_t launch_series_stats(const float* x, int64_t n, double* sum, cudaStream_t s);
 // fill = (float)(sum / n) on the device
 cudaError_t launch_fill_from_sum(const double* sum, int64_t n, float* fill, cudaStream_t s);
+// FP16 packing with a power-of-two scale per 4096 samples; scale needs n_blocks + 1
+// floats (the last receives the common scale, or 0)
 cudaError_t launch_f16_pack(const float* x, int64_t n, uint16_t* h, float* scale,
                             cudaStream_t s);
 

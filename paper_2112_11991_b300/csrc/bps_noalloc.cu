@@ -141,6 +141,8 @@ try {
     v.scale = nullptr;
     v.fill = (float)fill;
     v.fillp = nullptr;
+    v.uscalep = nullptr;
+    v.uscale = 0.f;
     if (launch_twiddle_init(tw, st) != cudaSuccess) return BPS_ERR_CUDA;
     k_store_template<<<1, 1, 0, st>>>(tv, dt);
     if (cudaGetLastError() != cudaSuccess) return BPS_ERR_CUDA;

@@ -102,6 +102,7 @@ __device__ __forceinline__ Anchor load_anchor(const Anchor* __restrict__ anc, in
 __device__ __forceinline__ void resolve_fill(SeriesView& x)
 {
     if (x.fillp) x.fill = __ldg(x.fillp);
+    x.uscale = x.uscalep ? __ldg(x.uscalep) : 0.f;
 }
 
 // Gathered sample x[idx] (the series mean outside [0, n)), FP32 or FP16+scale.
@@ -128,12 +129,21 @@ __device__ __forceinline__ void gather_f16_butterfly(const SeriesView& x, int n,
 {
     unsigned short hv[32];
     float sv[32];
+    if (x.uscale > 0.f) {  // all blocks share one scale: no per-sample scale loads
 #pragma unroll
-    for (int q = 0; q < 32; ++q) {
-        const int i = id[q];
-        const bool in = (unsigned)i < (unsigned)n;
-        hv[q] = in ? __ldg(x.f16 + i) : (unsigned short)0;
-        sv[q] = in ? __ldg(x.scale + (i >> 12)) : 0.f;
+        for (int q = 0; q < 32; ++q) {
+            const int i = id[q];
+            hv[q] = (unsigned)i < (unsigned)n ? __ldg(x.f16 + i) : (unsigned short)0;
+            sv[q] = x.uscale;
+        }
+    } else {
+#pragma unroll
+        for (int q = 0; q < 32; ++q) {
+            const int i = id[q];
+            const bool in = (unsigned)i < (unsigned)n;
+            hv[q] = in ? __ldg(x.f16 + i) : (unsigned short)0;
+            sv[q] = in ? __ldg(x.scale + (i >> 12)) : 0.f;
+        }
     }
 #pragma unroll
     for (int s = 0; s < 16; ++s) {

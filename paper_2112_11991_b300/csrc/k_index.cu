@@ -171,6 +171,10 @@ __global__ void k_f16_pack(const float* __restrict__ x, int64_t n, uint16_t* __r
             const float fr = frexpf(m, &ex);  // m = fr * 2^ex, fr in [0.5, 1)
             if (fr == 0.5f) ex -= 1;           // exact power of two: 2^(ex-1) = m
         }
+        // exponent rounded up to a multiple of 8: the block's largest |x| lands in
+        // (2^-8, 1], well inside the FP16 normal range, and blocks of similar amplitude
+        // share one scale (then the gather needs no per-sample scale load)
+        ex = ((ex + 7) >> 3) << 3;
         s_scale = ldexpf(1.f, ex);
         scale[blockIdx.x] = s_scale;
     }
@@ -224,10 +228,41 @@ cudaError_t launch_series_stats(const float* x, int64_t n, double* sum, cudaStre
     return cudaGetLastError();
 }
 
+// scale[nb] = the common scale of blocks 0..nb-1 when they all share it, else 0
+__global__ void k_scale_uniform(float* __restrict__ scale, int nb)
+{
+    __shared__ float smin[8], smax[8];
+    float lo = 3.4e38f, hi = 0.f;
+    for (int i = threadIdx.x; i < nb; i += blockDim.x) {
+        lo = fminf(lo, scale[i]);
+        hi = fmaxf(hi, scale[i]);
+    }
+    for (int o = 16; o > 0; o >>= 1) {
+        lo = fminf(lo, __shfl_down_sync(0xffffffffu, lo, o));
+        hi = fmaxf(hi, __shfl_down_sync(0xffffffffu, hi, o));
+    }
+    if ((threadIdx.x & 31) == 0) {
+        smin[threadIdx.x >> 5] = lo;
+        smax[threadIdx.x >> 5] = hi;
+    }
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        for (int w = 1; w < 8; ++w) {
+            lo = fminf(lo, smin[w]);
+            hi = fmaxf(hi, smax[w]);
+        }
+        lo = fminf(lo, smin[0]);
+        hi = fmaxf(hi, smax[0]);
+        scale[nb] = (lo == hi) ? lo : 0.f;
+    }
+}
+
 cudaError_t launch_f16_pack(const float* x, int64_t n, uint16_t* h, float* scale,
                             cudaStream_t s)
 {
-    k_f16_pack<<<(unsigned)((n + 4095) >> 12), 256, 0, s>>>(x, n, h, scale);
+    const int64_t nb = (n + 4095) >> 12;
+    k_f16_pack<<<(unsigned)nb, 256, 0, s>>>(x, n, h, scale);
+    k_scale_uniform<<<1, 256, 0, s>>>(scale, (int)nb);
     return cudaGetLastError();
 }
 
