@@ -93,16 +93,49 @@ __global__ void k_whitened(const float* __restrict__ Pw, Plan p, float* __restri
 }
 
 // Exact lower median (element of rank floor((W-1)/2), W = 32*VPL) of the FP32 values
-// held by one warp, VPL per lane: radix select over four digits of the bit pattern
-// (values >= 0: sign bit 0; digits = exponent [30:23], mantissa [22:15], [14:7], [6:0])
-// with the warp's padded 288-word shared histogram h (bin b at b + b/8: conflict-free
-// scan reads) and a warp prefix scan, no block barrier.  Returns the median's bits.
+// held by one warp, VPL per lane: radix select on the bit pattern (values >= 0: sign bit
+// 0) with the warp's padded 288-word shared histogram h (bin b at b + b/8: conflict-free
+// scan reads) and a warp prefix scan, no block barrier.  Digits: exponent [30:23],
+// mantissa [22:15], [14:7], [6:0].  The values left after the first two share the
+// median's top 16 bits (a relative width of 2^-8: one or two of 1024 for noise power);
+// when at most 32 are left they are gathered into h by ballot and each lane ranks its
+// own against them (ties counted, so the element of the remaining rank is found
+// exactly) instead of the last two digits.  Returns the median's bits.
 template <int VPL>
 __device__ __forceinline__ uint32_t warp_lower_median(const uint32_t (&u)[VPL], uint32_t* h, int lane)
 {
     uint32_t prefix = 0, pmask = 0, rank = (uint32_t)(32 * VPL - 1) / 2;
 #pragma unroll
     for (int pass = 0; pass < 4; ++pass) {
+        if (pass == 2) {
+            const uint32_t lt = (1u << lane) - 1u;
+            uint32_t m = 0;
+#pragma unroll
+            for (int i = 0; i < VPL; ++i) {
+                const bool c = (u[i] & pmask) == prefix;
+                const uint32_t b = __ballot_sync(0xffffffffu, c);
+                if (b) {
+                    const uint32_t pos = m + __popc(b & lt);
+                    if (c && pos < 32u) h[pos] = u[i];
+                    m += __popc(b);
+                }
+            }
+            __syncwarp();
+            if (m <= 32u) {
+                const uint32_t mine = (uint32_t)lane < m ? h[lane] : 0xffffffffu;
+                uint32_t less = 0, eq = 0;
+                for (uint32_t j = 0; j < m; ++j) {
+                    const uint32_t o = h[j];
+                    less += (o < mine) ? 1u : 0u;
+                    eq += (o == mine) ? 1u : 0u;
+                }
+                const bool own = (uint32_t)lane < m && less <= rank && rank < less + eq;
+                const int owner = __ffs(__ballot_sync(0xffffffffu, own)) - 1;
+                const uint32_t med = __shfl_sync(0xffffffffu, mine, owner);
+                __syncwarp();
+                return med;
+            }
+        }
         const int shift = pass == 0 ? 23 : pass == 1 ? 15 : pass == 2 ? 7 : 0;
         const uint32_t dm = pass == 3 ? 127u : 255u;
 #pragma unroll
@@ -156,7 +189,7 @@ __device__ __forceinline__ uint32_t warp_lower_median(const uint32_t (&u)[VPL], 
 // One warp per block of W = 32*VPL bins (bin order), values in registers; the block is
 // whitened in place: Pw = P * ln2 / med (0 when med = 0).
 template <int VPL>
-__global__ void __launch_bounds__(256) k_median_warp(float* __restrict__ P, Plan p,
+__global__ void __launch_bounds__(256, 4) k_median_warp(float* __restrict__ P, Plan p,
                                                      float* __restrict__ scale)
 {
     __shared__ uint32_t hist[8][288];
@@ -178,13 +211,13 @@ __global__ void __launch_bounds__(256) k_median_warp(float* __restrict__ P, Plan
 
 // The same from pass 2's row-major-by-k1 power Pt[k1 C + k2] (bin k1 + R k2, W <= R):
 // a CTA of kMedCols warps takes the kMedCols blocks at k2 in [k20, k20 + kMedCols),
-// k1 in [q0, q0 + W) -- W row segments of 64 bytes -- into a shared tile padded to
+// k1 in [q0, q0 + W) -- W row segments of 32 bytes -- into a shared tile padded to
 // kMedCols + 1 words per row (conflict-free column reads); warp w takes the median of
-// column k20 + w and writes its whitened block to P in bin order.  (Measured at
-// C = 4096: 64-byte segments with two CTAs per SM beat 32-byte segments with four and
-// 128-byte segments with one.)
-constexpr int kMedCols = 16;
-constexpr int kLogMedCols = 4;
+// column k20 + w and writes its whitened block to P in bin order.  (Measured at C = 2048
+// and 4096: 32-byte segments with four CTAs per SM beat 64-byte segments with two, whose
+// 16 warps need more than 64 registers with the candidate gather of the median.)
+constexpr int kMedCols = 8;
+constexpr int kLogMedCols = 3;
 
 template <int VPL>
 __global__ void __launch_bounds__(32 * kMedCols) k_median_warp_t(const float* __restrict__ Pt, Plan p,
