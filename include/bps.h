@@ -181,6 +181,28 @@ int bps_harmonic_sums(bps_ctx* ctx, int64_t series_id, int64_t bank_id,
                       int64_t template_idx, const bps_search_params* params,
                       float* s_out);
 
+/* Whitening of caller-provided power spectra with the search's own block-median
+ * kernels (App. A, "Fourier de-reddening"): for spectrum s in [0, count) and block b
+ * of W = whiten_block consecutive bins, med_b is the block's lower median (its
+ * element of rank floor((W-1)/2), counted from 0 in ascending order) and
+ *   d_scale_out[s * nbins/W + b] = ln2 / med_b      (FP32 division; 0 when med_b = 0)
+ *   d_pw_out[s * nbins + k]      = d_power[s * nbins + k] * scale of k's block
+ *                                                     (one FP32 product)
+ *   d_power      device memory of the context's GPU, count * nbins floats, read
+ *                only; values >= 0 and not NaN (other values give an unspecified
+ *                result, never a fault)
+ *   count        number of spectra, >= 1
+ *   nbins        bins per spectrum, a power of two in [whiten_block, 2^30]
+ *   whiten_block power of two in [32, 8192]
+ *   d_pw_out     device, count * nbins floats; equal to d_power (in place) or not
+ *                overlapping it
+ *   d_scale_out  device, count * nbins / whiten_block floats
+ *   cuda_stream  cudaStream_t to run on (NULL = legacy default stream)
+ * Returns BPS_OK, BPS_ERR_INVALID_ARG or BPS_ERR_CUDA; the work is enqueued on the
+ * stream and the call does not wait for it.  No device memory is allocated. */
+int bps_whiten(bps_ctx* ctx, const float* d_power, int64_t count, int64_t nbins,
+               int32_t whiten_block, float* d_pw_out, float* d_scale_out, void* cuda_stream);
+
 /* ---- measurement ------------------------------------------------------------ */
 
 /* Stage indices of bps_stats.stage_ms / stage_launches. */

@@ -42,7 +42,7 @@ EXPORTED = ["bps_default_params", "bps_create", "bps_destroy", "bps_load_series"
             "bps_server_last_error", "bps_autotune", "bps_distill", "bps_series_update",
             "bps_graph_create", "bps_graph_launch", "bps_graph_fetch", "bps_default_bank_spec",
             "bps_metric_density", "bps_metric_projected", "bps_metric_bank",
-            "bps_selftest_bounded_wait"]
+            "bps_selftest_bounded_wait", "bps_whiten"]
 STAGES = ["anchors", "pass1", "pass2", "power", "median", "harmsum"]
 
 
@@ -170,6 +170,8 @@ def lib():
         L.bps_graph_fetch.argtypes = [vp, i64, i64, vp, i64, P(i64), P(i64)]
         L.bps_selftest_bounded_wait.restype = i32
         L.bps_selftest_bounded_wait.argtypes = [vp, i32, P(i32)]
+        L.bps_whiten.restype = i32
+        L.bps_whiten.argtypes = [vp, vp, i64, i64, i32, vp, vp, vp]
         L.bps_default_bank_spec.restype = None
         L.bps_default_bank_spec.argtypes = [P(bps_bank_spec)]
         L.bps_metric_density.restype = i32
@@ -451,6 +453,32 @@ class Context:
                     "bps_selftest_bounded_wait")
         return bool(t.value)
 
+    def whiten(self, power, whiten_block: int = 1024, stream=None, out=None):
+        """Block-median whitening of caller-provided power spectra on the device
+        (bps_whiten): power is a contiguous float32 CUDA tensor of shape (count, nbins)
+        or (nbins,); returns (Pw, scale) with scale = ln2 / block median per block.
+        out=power whitens in place.  Runs on `stream` (default: the current torch
+        stream) and does not wait."""
+        import torch
+        if not (isinstance(power, torch.Tensor) and power.is_cuda and
+                power.dtype == torch.float32 and power.is_contiguous()):
+            raise TypeError("power must be a contiguous float32 CUDA tensor")
+        pw2 = power.reshape(-1, power.shape[-1])
+        count, nbins = pw2.shape
+        pw = torch.empty_like(power) if out is None else out
+        if not (pw.is_cuda and pw.dtype == torch.float32 and pw.is_contiguous() and
+                pw.shape == power.shape):
+            raise TypeError("out must match power")
+        scale = torch.empty(power.shape[:-1] + (max(nbins // int(whiten_block), 1),),
+                            dtype=torch.float32, device=power.device)
+        if stream is None:
+            stream = torch.cuda.current_stream(power.device)
+        rc = lib().bps_whiten(self.h, C.c_void_p(power.data_ptr()), int(count), int(nbins),
+                              int(whiten_block), C.c_void_p(pw.data_ptr()),
+                              C.c_void_p(scale.data_ptr()), _stream_ptr(stream))
+        self._check(rc, "bps_whiten")
+        return pw, scale
+
     def set_profiling(self, on: bool):
         self._check(lib().bps_set_profiling(self.h, int(bool(on))), "bps_set_profiling")
 
@@ -651,6 +679,11 @@ def bps_set_profiling(ctx, on):
 
 def bps_selftest_bounded_wait(ctx, limit, timed_out):
     return lib().bps_selftest_bounded_wait(ctx, limit, timed_out)
+
+
+def bps_whiten(ctx, d_power, count, nbins, whiten_block, d_pw_out, d_scale_out, stream):
+    return lib().bps_whiten(ctx, d_power, count, nbins, whiten_block, d_pw_out, d_scale_out,
+                            stream)
 
 
 def bps_default_bank_spec(spec):

@@ -1297,6 +1297,55 @@ try {
     return BPS_ERR_OUT_OF_MEMORY;  // host allocation failed
 }
 
+int bps_whiten(bps_ctx* ctx, const float* d_power, int64_t count, int64_t nbins,
+               int32_t whiten_block, float* d_pw_out, float* d_scale_out, void* cuda_stream)
+try {
+    if (!ctx) return BPS_ERR_INVALID_ARG;
+    std::lock_guard<std::recursive_mutex> lk(ctx->mu);
+    const int logW = ilog2(whiten_block);
+    const int logM = ilog2(nbins);
+    if (whiten_block < 32 || whiten_block > 8192 || (1ll << logW) != whiten_block)
+        return fail(ctx, BPS_ERR_INVALID_ARG, "whiten_block %d: not a power of two in [32, 8192]",
+                    whiten_block);
+    if (nbins < whiten_block || nbins > (1ll << 30) || (1ll << logM) != nbins)
+        return fail(ctx, BPS_ERR_INVALID_ARG, "nbins %lld: not a power of two in [whiten_block, 2^30]",
+                    (long long)nbins);
+    if (count < 1 || !d_power || !d_pw_out || !d_scale_out)
+        return fail(ctx, BPS_ERR_INVALID_ARG, "bad count or null pointer");
+    const int64_t nblk = nbins >> logW;
+    const size_t bytes = sizeof(float) * (size_t)count * (size_t)nbins;
+    const void* ptrs[3] = {d_power, d_pw_out, d_scale_out};
+    for (const void* q : ptrs) {
+        cudaPointerAttributes a;
+        if (cudaPointerGetAttributes(&a, q) != cudaSuccess) {
+            cudaGetLastError();
+            return fail(ctx, BPS_ERR_INVALID_ARG, "not a device pointer");
+        }
+        if (!(a.type == cudaMemoryTypeManaged ||
+              (a.type == cudaMemoryTypeDevice && a.device == ctx->device)))
+            return fail(ctx, BPS_ERR_INVALID_ARG, "not device memory of the context's GPU");
+    }
+    const char* pin = (const char*)d_power;
+    const char* pout = (const char*)d_pw_out;
+    if (pin != pout && pin < pout + bytes && pout < pin + bytes)
+        return fail(ctx, BPS_ERR_INVALID_ARG, "d_pw_out overlaps d_power");
+    CK(cudaSetDevice(ctx->device));
+    cudaStream_t st = (cudaStream_t)cuda_stream;
+    if (pin != pout) CK(cudaMemcpyAsync(d_pw_out, d_power, bytes, cudaMemcpyDeviceToDevice, st));
+    Plan p{};
+    p.M = nbins;
+    p.logM = logM;
+    p.logW = logW;
+    p.ptrans = 0;
+    for (int64_t s0 = 0; s0 < count; s0 += 65535) {
+        const int nt = (int)std::min<int64_t>(65535, count - s0);
+        CK(launch_block_median(d_pw_out + s0 * nbins, nt, p, d_scale_out + s0 * nblk, st));
+    }
+    return BPS_OK;
+} catch (...) {
+    return BPS_ERR_OUT_OF_MEMORY;  // host allocation failed
+}
+
 }  // extern "C"
 
 // =====================================================================================
