@@ -212,10 +212,13 @@ int make_plan(bps_ctx* ctx, const Series& s, const Bank& b, const bps_search_par
     plan_geometry(p, pr.log_tile ? pr.log_tile : t1, pr.log_tile2 ? pr.log_tile2 : t2,
                   pr.log_cols ? pr.log_cols : lc);
     p.logW = ilog2(pr.whiten_block);
-    // transposed power when a whitening block lies within one k2 (W <= R) and the warp
-    // median applies (W <= 1024): pass 2 then writes whole rows
-    p.ptrans = (pr.mode == BPS_MODE_FUSED && p.logW <= 10 && p.logW <= p.logR && p.logNP <= 6 &&
-                p.logC >= 12) ? 1 : 0;
+    // row-major power (in groups of NP rows) when a pass-2 CTA holds at most two row pairs,
+    // whose bin-order stores would be runs of one or two words, a whitening block lies
+    // within one k2 (W <= R) and the warp median applies (W <= 1024).  Measured at 2^23,
+    // C = 2048: NP = 2 pass 2 + median 14.5 + 7.7 us (bin order 21.1 + 5.4); NP = 4
+    // 17.0 + 7.4 (bin order 18.5 + 5.4).
+    p.ptrans = (pr.mode == BPS_MODE_FUSED && p.logW <= 10 && p.logW <= p.logR && p.logNP <= 1)
+                   ? 1 : 0;
     p.nharm = pr.nharm_max;
     p.lognh = ilog2(pr.nharm_max);
     p.nlev = p.lognh + 1;

@@ -209,13 +209,14 @@ __global__ void __launch_bounds__(256, 4) k_median_warp(float* __restrict__ P, P
     if (lane == 0) scale[(int64_t)tl * nblk + blk] = sc;
 }
 
-// The same from pass 2's row-major-by-k1 power Pt[k1 C + k2] (bin k1 + R k2, W <= R):
-// a CTA of kMedCols warps takes the kMedCols blocks at k2 in [k20, k20 + kMedCols),
-// k1 in [q0, q0 + W) -- W row segments of 32 bytes -- into a shared tile padded to
-// kMedCols + 1 words per row (conflict-free column reads); warp w takes the median of
-// column k20 + w and writes its whitened block to P in bin order.  (Measured at C = 2048
-// and 4096: 32-byte segments with four CTAs per SM beat 64-byte segments with two, whose
-// 16 warps need more than 64 registers with the candidate gather of the median.)
+// The same from pass 2's row-major power in groups of T = NP rows (bin k1 + R k2 at
+// Pt[(k1 div T) T C + k2 T + k1 mod T], W <= R, T <= W): a CTA of kMedCols warps takes
+// the kMedCols blocks at k2 in [k20, k20 + kMedCols), k1 in [q0, q0 + W) -- W/T runs of
+// 4 kMedCols T bytes -- into a shared tile padded to kMedCols + 1 words per row
+// (conflict-free column reads); warp w takes the median of column k20 + w and writes its
+// whitened block to P in bin order.  (Measured with T = 1 at C = 2048 and 4096: 32-byte
+// runs with four CTAs per SM beat 64-byte runs with two, whose 16 warps need more than
+// 64 registers with the candidate gather of the median.)
 constexpr int kMedCols = 8;
 constexpr int kLogMedCols = 3;
 
@@ -236,15 +237,20 @@ __global__ void __launch_bounds__(32 * kMedCols) k_median_warp_t(const float* __
     const int qb = (int)(blockIdx.x >> lg);
     const int q0 = qb * W;
     const float* src = Pt + (int64_t)tl * p.M;
-    constexpr int F4 = kMedCols / 4;  // float4 per row segment
-    for (int i = threadIdx.x; i < F4 * W; i += blockDim.x) {
-        const int r = i / F4, f = i % F4;
-        const float4 v = __ldg(reinterpret_cast<const float4*>(src + ((int64_t)(q0 + r) << p.logC) + k20 + 4 * f));
-        uint32_t* t = tile + r * TS + 4 * f;
-        t[0] = __float_as_uint(v.x);
-        t[1] = __float_as_uint(v.y);
-        t[2] = __float_as_uint(v.z);
-        t[3] = __float_as_uint(v.w);
+    const int logT = p.logNP;
+    const int lch = kLogMedCols + logT;  // log2 of the floats of one group's kMedCols columns
+    const float* g0 = src + ((int64_t)(q0 >> logT) << (logT + p.logC)) + ((int64_t)k20 << logT);
+    for (int i = threadIdx.x; i < (W * kMedCols) / 4; i += blockDim.x) {
+        const int f = 4 * i;
+        const int gi = f >> lch, o = f & ((1 << lch) - 1);
+        const float4 v =
+            __ldg(reinterpret_cast<const float4*>(g0 + ((int64_t)gi << (logT + p.logC)) + o));
+        const float e[4] = {v.x, v.y, v.z, v.w};
+#pragma unroll
+        for (int u = 0; u < 4; ++u) {
+            const int c = (o + u) >> logT, r = (gi << logT) + ((o + u) & ((1 << logT) - 1));
+            tile[r * TS + c] = __float_as_uint(e[u]);
+        }
     }
     __syncthreads();
     uint32_t u[VPL];
@@ -548,7 +554,8 @@ cudaError_t launch_block_median(float* P, int nt, const Plan& p, float* scale,
 {
     const int64_t nblk = p.M >> p.logW;
     if (p.ptrans) {
-        if (!Pt || p.logW > 10 || p.logW > p.logR || p.logC < kLogMedCols) return cudaErrorInvalidValue;
+        if (!Pt || p.logW > 10 || p.logW > p.logR || p.logC < kLogMedCols || p.logNP > p.logW)
+            return cudaErrorInvalidValue;
         cudaError_t e = med_t_attributes();
         if (e != cudaSuccess) return e;
         dim3 tgrid((unsigned)(nblk / kMedCols), (unsigned)nt);

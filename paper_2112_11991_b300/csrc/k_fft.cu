@@ -425,7 +425,7 @@ __global__ void __launch_bounds__(1024, 1) k_pass2(const float2* __restrict__ Y,
     // slack in all).  The first radix-16 stage (Ns = 1) is fused with the load:
     // butterfly (line, j) reads elements j + s C/16 of its row straight from Y.
     const int skew = logNP <= 4 ? (16 >> logNP) : (logNP == 5 ? 1 : 0);
-    // W_N^q of the NP low rows, for the row-major power layout (plan.ptrans, NP <= 64);
+    // W_N^q of the NP low rows, for the row-major power layout (plan.ptrans, NP <= 2);
     // visible to all after the first-stage barrier
     __shared__ float2 s_wq[64];
     if (p.ptrans && (int)threadIdx.x < NP)
@@ -461,12 +461,19 @@ __global__ void __launch_bounds__(1024, 1) k_pass2(const float2* __restrict__ Y,
     }
     float* Pt = P + (int64_t)tl * M;
     if (p.ptrans) {
-        // row-major power: P'[q C + k2] holds bin q + R k2.  Items k2-fastest, so a warp
-        // reads consecutive elements of one line and writes consecutive words of a row.
+        // row-major power in groups of NP rows, column-major inside a group: bin k1 + R k2
+        // at P'[(k1 div NP) NP C + k2 NP + k1 mod NP], so this CTA's low rows are one
+        // contiguous NP C run (their mirrors straddle two groups).  Items q-fastest: a
+        // warp's low-row stores fill whole lines; the median kernel reads 8 columns of a
+        // group as one 32 NP-byte run.
         const int twsh = 12 - logC;
         const int items = NP * C;
+        const auto at_ = [&](int k1, int k2) -> int64_t {
+            return ((int64_t)(k1 >> logNP) << (logNP + logC)) + ((int64_t)k2 << logNP) +
+                   (k1 & (NP - 1));
+        };
         for (int it = threadIdx.x; it < items; it += nthr) {
-            const int ql = it >> logC, k2 = it & (C - 1);
+            const int ql = it & (NP - 1), k2 = it >> logNP;
             const int q = q0 + ql;
             const int lowl = ql, highl = NP + ql;
             const int lo0 = lowl * skew, hi0 = highl * skew;
@@ -475,8 +482,8 @@ __global__ void __launch_bounds__(1024, 1) k_pass2(const float2* __restrict__ Y,
                 const float2 w = cmul(s_wq[ql], __ldg(tw + (k2 << twsh)));
                 power_pair(sm[pad(lowl * C + k2) + lo0], sm[pad(highl * C + (C - 1 - k2)) + hi0], w,
                            pa, pb);
-                Pt[((int64_t)q << logC) + k2] = pa;
-                Pt[((int64_t)(R - q) << logC) + (C - 1 - k2)] = pb;
+                Pt[at_(q, k2)] = pa;
+                Pt[at_(R - q, C - 1 - k2)] = pb;
             } else {
                 if (k2 <= (C >> 1)) {  // row 0: bins R k2 and M - R k2 = R (C - k2)
                     power_pair(sm[pad(k2) + lo0], sm[pad((C - k2) & (C - 1)) + lo0],
@@ -484,8 +491,8 @@ __global__ void __launch_bounds__(1024, 1) k_pass2(const float2* __restrict__ Y,
                     if (k2 == 0) {
                         Pt[0] = 0.f;
                     } else {
-                        Pt[k2] = pa;
-                        if (k2 != (C >> 1)) Pt[C - k2] = pb;
+                        Pt[at_(0, k2)] = pa;
+                        if (k2 != (C >> 1)) Pt[at_(0, C - k2)] = pb;
                     }
                 }
                 if (k2 < (C >> 1)) {  // row R/2: bins R/2 + R k2 and R/2 + R (C - 1 - k2)
@@ -493,8 +500,8 @@ __global__ void __launch_bounds__(1024, 1) k_pass2(const float2* __restrict__ Y,
                         cmul(twiddle((uint32_t)(R >> 1), logn), __ldg(tw + (k2 << twsh)));
                     power_pair(sm[pad(highl * C + k2) + hi0],
                                sm[pad(highl * C + (C - 1 - k2)) + hi0], w, pa, pb);
-                    Pt[((int64_t)(R >> 1) << logC) + k2] = pa;
-                    Pt[((int64_t)(R >> 1) << logC) + (C - 1 - k2)] = pb;
+                    Pt[at_(R >> 1, k2)] = pa;
+                    Pt[at_(R >> 1, C - 1 - k2)] = pb;
                 }
             }
         }
