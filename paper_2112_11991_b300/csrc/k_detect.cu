@@ -220,7 +220,7 @@ __global__ void __launch_bounds__(256, 4) k_median_warp(float* __restrict__ P, P
 constexpr int kMedCols = 8;
 constexpr int kLogMedCols = 3;
 
-template <int VPL>
+template <int VPL, int LOGT>
 __global__ void __launch_bounds__(32 * kMedCols) k_median_warp_t(const float* __restrict__ Pt, Plan p,
                                                                    float* __restrict__ P,
                                                                    float* __restrict__ scale)
@@ -237,18 +237,18 @@ __global__ void __launch_bounds__(32 * kMedCols) k_median_warp_t(const float* __
     const int qb = (int)(blockIdx.x >> lg);
     const int q0 = qb * W;
     const float* src = Pt + (int64_t)tl * p.M;
-    const int logT = p.logNP;
-    const int lch = kLogMedCols + logT;  // log2 of the floats of one group's kMedCols columns
-    const float* g0 = src + ((int64_t)(q0 >> logT) << (logT + p.logC)) + ((int64_t)k20 << logT);
-    for (int i = threadIdx.x; i < (W * kMedCols) / 4; i += blockDim.x) {
+    constexpr int LCH = kLogMedCols + LOGT;  // log2 of the floats of one group's kMedCols columns
+    const float* g0 = src + ((int64_t)(q0 >> LOGT) << (LOGT + p.logC)) + ((int64_t)k20 << LOGT);
+#pragma unroll 4
+    for (int i = threadIdx.x; i < (W * kMedCols) / 4; i += 32 * kMedCols) {
         const int f = 4 * i;
-        const int gi = f >> lch, o = f & ((1 << lch) - 1);
+        const int gi = f >> LCH, o = f & ((1 << LCH) - 1);
         const float4 v =
-            __ldg(reinterpret_cast<const float4*>(g0 + ((int64_t)gi << (logT + p.logC)) + o));
+            __ldg(reinterpret_cast<const float4*>(g0 + ((int64_t)gi << (LOGT + p.logC)) + o));
         const float e[4] = {v.x, v.y, v.z, v.w};
 #pragma unroll
         for (int u = 0; u < 4; ++u) {
-            const int c = (o + u) >> logT, r = (gi << logT) + ((o + u) & ((1 << logT) - 1));
+            const int c = (o + u) >> LOGT, r = (gi << LOGT) + ((o + u) & ((1 << LOGT) - 1));
             tile[r * TS + c] = __float_as_uint(e[u]);
         }
     }
@@ -539,9 +539,13 @@ cudaError_t med_t_attributes()
     if (dev < 0 || dev >= 64) return cudaErrorInvalidDevice;
     std::lock_guard<std::mutex> lk(mu);
     if (done[dev]) return cudaSuccess;
-#define BPS_MED_ATTR(v) \
-    if (e == cudaSuccess)  \
-        e = cudaFuncSetAttribute(k_median_warp_t<v>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)med_t_smem<v>());
+#define BPS_MED_ATTR(v)                                                                             \
+    if (e == cudaSuccess)                                                                           \
+        e = cudaFuncSetAttribute(k_median_warp_t<v, 0>, cudaFuncAttributeMaxDynamicSharedMemorySize, \
+                                 (int)med_t_smem<v>());                                             \
+    if (e == cudaSuccess)                                                                           \
+        e = cudaFuncSetAttribute(k_median_warp_t<v, 1>, cudaFuncAttributeMaxDynamicSharedMemorySize, \
+                                 (int)med_t_smem<v>());
     BPS_MED_ATTR(1) BPS_MED_ATTR(2) BPS_MED_ATTR(4) BPS_MED_ATTR(8) BPS_MED_ATTR(16) BPS_MED_ATTR(32)
 #undef BPS_MED_ATTR
     if (e == cudaSuccess) done[dev] = true;
@@ -554,20 +558,29 @@ cudaError_t launch_block_median(float* P, int nt, const Plan& p, float* scale,
 {
     const int64_t nblk = p.M >> p.logW;
     if (p.ptrans) {
-        if (!Pt || p.logW > 10 || p.logW > p.logR || p.logC < kLogMedCols || p.logNP > p.logW)
+        if (!Pt || p.logW > 10 || p.logW > p.logR || p.logC < kLogMedCols || p.logNP > 1)
             return cudaErrorInvalidValue;
         cudaError_t e = med_t_attributes();
         if (e != cudaSuccess) return e;
         dim3 tgrid((unsigned)(nblk / kMedCols), (unsigned)nt);
         const int th = 32 * kMedCols;
-        switch (p.logW) {
-            case 5: k_median_warp_t<1><<<tgrid, th, med_t_smem<1>(), s>>>(Pt, p, P, scale); break;
-            case 6: k_median_warp_t<2><<<tgrid, th, med_t_smem<2>(), s>>>(Pt, p, P, scale); break;
-            case 7: k_median_warp_t<4><<<tgrid, th, med_t_smem<4>(), s>>>(Pt, p, P, scale); break;
-            case 8: k_median_warp_t<8><<<tgrid, th, med_t_smem<8>(), s>>>(Pt, p, P, scale); break;
-            case 9: k_median_warp_t<16><<<tgrid, th, med_t_smem<16>(), s>>>(Pt, p, P, scale); break;
-            default: k_median_warp_t<32><<<tgrid, th, med_t_smem<32>(), s>>>(Pt, p, P, scale); break;
+#define BPS_MED_T(v, lt) k_median_warp_t<v, lt><<<tgrid, th, med_t_smem<v>(), s>>>(Pt, p, P, scale)
+#define BPS_MED_T_W(lt)                    \
+    switch (p.logW) {                      \
+        case 5: BPS_MED_T(1, lt); break;   \
+        case 6: BPS_MED_T(2, lt); break;   \
+        case 7: BPS_MED_T(4, lt); break;   \
+        case 8: BPS_MED_T(8, lt); break;   \
+        case 9: BPS_MED_T(16, lt); break;  \
+        default: BPS_MED_T(32, lt); break; \
+    }
+        if (p.logNP == 0) {
+            BPS_MED_T_W(0)
+        } else {
+            BPS_MED_T_W(1)
         }
+#undef BPS_MED_T_W
+#undef BPS_MED_T
         return cudaGetLastError();
     }
     dim3 wgrid((unsigned)((nblk + 7) / 8), (unsigned)nt);
