@@ -1313,7 +1313,7 @@ try {
     if (nbins < whiten_block || nbins > (1ll << 30) || (1ll << logM) != nbins)
         return fail(ctx, BPS_ERR_INVALID_ARG, "nbins %lld: not a power of two in [whiten_block, 2^30]",
                     (long long)nbins);
-    if (count < 1 || !d_power || !d_pw_out || !d_scale_out)
+    if (count < 1 || count > (INT64_MAX / 4) / nbins || !d_power || !d_pw_out || !d_scale_out)
         return fail(ctx, BPS_ERR_INVALID_ARG, "bad count or null pointer");
     const int64_t nblk = nbins >> logW;
     const size_t bytes = sizeof(float) * (size_t)count * (size_t)nbins;

@@ -137,7 +137,7 @@ def test_whiten_arguments(bps, ctx):
 
     assert call(**ok) == bps.BPS_OK
     for bad in (dict(W=16), dict(W=16384), dict(W=48), dict(nbins=16), dict(nbins=3000),
-                dict(count=0), dict(out=d[1:]), dict(scale=None)):
+                dict(count=0), dict(count=1 << 61), dict(out=d[1:]), dict(scale=None)):
         assert call(**bad) == bps.BPS_ERR_INVALID_ARG, bad
     host = np.zeros(1 << 12, np.float32)
     assert call(src=host.ctypes.data_as(vp)) == bps.BPS_ERR_INVALID_ARG
