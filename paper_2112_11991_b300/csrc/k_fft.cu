@@ -467,12 +467,14 @@ __global__ void __launch_bounds__(1024, 1) k_pass2(const float2* __restrict__ Y,
         // warp's low-row stores fill whole lines; the median kernel reads 8 columns of a
         // group as one 32 NP-byte run.
         const int twsh = 12 - logC;
-        const int items = NP * C;
         const auto at_ = [&](int k1, int k2) -> int64_t {
             return ((int64_t)(k1 >> logNP) << (logNP + logC)) + ((int64_t)k2 << logNP) +
                    (k1 & (NP - 1));
         };
-        for (int it = threadIdx.x; it < items; it += nthr) {
+        static_assert(kEPT2 % 2 == 0, "items per thread");
+#pragma unroll
+        for (int r = 0; r < kEPT2 / 2; ++r) {  // items = NP C = (kEPT2 / 2) nthr
+            const int it = (int)threadIdx.x + r * nthr;
             const int ql = it & (NP - 1), k2 = it >> logNP;
             const int q = q0 + ql;
             const int lowl = ql, highl = NP + ql;
@@ -514,8 +516,9 @@ __global__ void __launch_bounds__(1024, 1) k_pass2(const float2* __restrict__ Y,
     const int twsh = 12 - logC;
     const int lowl = ql, highl = NP + ql;
     const int lo0 = lowl * skew, hi0 = highl * skew;
-    const int items = NP * C;
-    for (int it = threadIdx.x; it < items; it += nthr) {
+#pragma unroll
+    for (int r = 0; r < kEPT2 / 2; ++r) {  // items = NP C = (kEPT2 / 2) nthr
+        const int it = (int)threadIdx.x + r * nthr;
         const int k2 = it >> logNP;
         if (q != 0) {
             const int64_t k = q + ((int64_t)k2 << logR);
