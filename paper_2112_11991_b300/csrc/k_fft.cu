@@ -254,11 +254,20 @@ __device__ __forceinline__ void pass1_last_stage(const float2* __restrict__ sm, 
             st[s] = cmul(st[hb], st[s - hb]);
         }
     }
+    // W_M^{j2 j} of the thread's butterflies: j steps by nthr / G, so with more than two
+    // butterflies the later ones take one product each instead of a sincospi
+    float2 u0, du;
+    if (BPT > 2) {
+        u0 = twiddle((j2 * (uint32_t)(threadIdx.x >> logG)) & Mm, logM);
+        du = twiddle((j2 * (uint32_t)(nthr >> logG)) & Mm, logM);
+    }
 #pragma unroll
     for (int i = 0; i < BPT; ++i) {
         const int b = threadIdx.x + i * nthr;
         const int g = b & (G - 1);
         const int j = b >> logG;
+        if (BPT <= 2) u0 = twiddle((j2 * (uint32_t)j) & Mm, logM);
+        else if (i > 0) u0 = cmul(u0, du);
         float2 v[RL];
 #pragma unroll
         for (int s = 0; s < RL; ++s) v[s] = sm[pad(g + G * (j + s * Ns))];
@@ -275,7 +284,7 @@ __device__ __forceinline__ void pass1_last_stage(const float2* __restrict__ sm, 
         }
         Radix<LOGR_LAST>::dft(v);
         float2 u[RL];
-        u[0] = twiddle((j2 * (uint32_t)j) & Mm, logM);
+        u[0] = u0;
 #pragma unroll
         for (int s = 1; s < RL; ++s) u[s] = cmul(u[0], st[s]);
 #pragma unroll
