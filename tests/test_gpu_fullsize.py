@@ -52,10 +52,16 @@ def _recovered(cands, T, period, thr):
 
 
 def test_htru_2p23_full_bank_sampled(bps, ctx, orc):
+    """The whole 2^23 x 4096 request in the launch configuration the benchmark times: the
+    autotuner's choice on a 64-template sample (four-step split, tiles, batch -- and with
+    them the power layout), which later searches of this size use."""
     w = synth.htru_circular()
     sid = ctx.load_series(w.series, w.tsamp)
     bid = ctx.load_bank(w.bank)
     prm = bps.default_params(cand_cap=1 << 24)
+    best, _ = ctx.autotune(sid, bid, prm, sample_templates=64)
+    print("\n[shape] 2^23 autotuned: C = 2^%d, tiles %d/%d, batch %d"
+          % (best.log_cols, best.log_tile, best.log_tile2, best.batch))
     gc, total = ctx.fetch_candidates(ctx.search(sid, bid, prm))
     assert total == gc.size
     thr = bps.thresholds(prm, w.n, w.bank.shape[0])

@@ -343,11 +343,13 @@ def test_bounded_wait_expires_and_context_survives(bps, ctx, w1):
 
 
 @pytest.mark.parametrize("logn,log_cols,W", [(16, 9, 1024), (18, 9, 1024), (18, 11, 1024),
-                                             (20, 11, 1024), (20, 12, 1024), (21, 12, 256)])
+                                             (20, 11, 1024), (20, 12, 1024), (21, 12, 256),
+                                             (22, 11, 1024)])
 def test_four_step_splits_against_oracle(bps, ctx, orc, logn, log_cols, W):
     """Other four-step splits N/2 = R x C (other radix structures of both FFT passes;
-    with C = 4096 and W <= R the row-major power layout and the transposing median)
-    give the oracle's whitened power and candidates."""
+    where a pass-2 CTA holds one or two row pairs and W <= R -- 2^21 with C = 4096, 2^22
+    with C = 2048 -- the grouped row-major power layout and the transposing median) give
+    the oracle's whitened power and candidates."""
     n, ts = 1 << logn, 64e-6
     T = n * ts
     p = synth.Pulsar(period_s=0.023, porb_s=6 * T, tau_lts=0.06, phi_rad=0.9, amp=0.4)
