@@ -466,13 +466,11 @@ struct Job {
         return ws_alloc(ctx, p, nt, mode, st, w, (int)chunk);
     }
 
+    // device bytes of the workspace setup() allocates (the carve's own count, so the
+    // row-major power buffer of plan.ptrans is included)
     static size_t workspace_bytes(const Plan& p, int nt, int64_t chunk, int mode)
     {
-        return align256(sizeof(Anchor) * (size_t)p.nanchor * chunk) +
-               align256(sizeof(float2) * (size_t)(p.M + 1) * nt) +
-               (mode == BPS_MODE_PLAIN ? align256(sizeof(float) * (size_t)p.n * nt) : 0) +
-               align256(sizeof(float) * (size_t)p.M * nt) +
-               align256(sizeof(float) * (size_t)(p.M >> p.logW) * nt);
+        return ws_carve(p, nt, mode, (int)chunk, nullptr, nullptr);
     }
 
     int issue_batch()
