@@ -10,7 +10,8 @@ HERE = os.path.dirname(os.path.abspath(__file__))
 ROOT = os.path.dirname(HERE)
 LIB = os.path.join(HERE, "libbps.so")
 SOURCES = sorted(glob.glob(os.path.join(HERE, "csrc", "*.cu")))
-DEPS = SOURCES + sorted(glob.glob(os.path.join(HERE, "csrc", "*.cuh"))) + [
+DEPS = SOURCES + sorted(glob.glob(os.path.join(HERE, "csrc", "*.cuh"))) + \
+    sorted(glob.glob(os.path.join(HERE, "csrc", "*.h"))) + [
     os.path.join(ROOT, "include", "bps.h")]
 
 NVCC_FLAGS = ["-gencode", "arch=compute_103a,code=sm_103a", "-O3", "-lineinfo",
