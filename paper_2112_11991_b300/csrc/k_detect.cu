@@ -209,7 +209,7 @@ __global__ void __launch_bounds__(256, 4) k_median_warp(float* __restrict__ P, P
     if (lane == 0) scale[(int64_t)tl * nblk + blk] = sc;
 }
 
-// The same from pass 2's row-major power in groups of T = NP rows (bin k1 + R k2 at
+// The same from pass 2's row-major power in groups of T = NP = 2^LOGT rows (bin k1 + R k2 at
 // Pt[(k1 div T) T C + k2 T + k1 mod T], W <= R, T <= W): a CTA of kMedCols warps takes
 // the kMedCols blocks at k2 in [k20, k20 + kMedCols), k1 in [q0, q0 + W) -- W/T runs of
 // 4 kMedCols T bytes -- into a shared tile padded to kMedCols + 1 words per row
@@ -354,7 +354,8 @@ __device__ __forceinline__ void mbar_arrive(uint64_t* bar)
 // the stage's "full" mbarrier); 8 consumer warps sum, threshold and compact, then release
 // the stage on its "empty" mbarrier.  CTAs are persistent over tiles j = blockIdx.x +
 // i gridDim.x.  Two stages (70 KB) let three CTAs share an SM: measured at 2^23, 9.9 us per
-// template against 10.4 with three stages and two CTAs, 18.2 with four stages and one.  Every wait is bounded: on expiry the status word is flagged (reported as
+// template against 10.4 with three stages and two CTAs, 18.2 with four stages and one.
+// Every wait is bounded: on expiry the status word is flagged (reported as
 // BPS_ERR_TIMEOUT) and the warp leaves after a bounded drain of its copies in flight.
 constexpr int kHsTile = 1024;
 constexpr int kHsConsumerWarps = 8;
