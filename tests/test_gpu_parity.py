@@ -344,7 +344,7 @@ def test_bounded_wait_expires_and_context_survives(bps, ctx, w1):
 
 @pytest.mark.parametrize("logn,log_cols,W", [(16, 9, 1024), (18, 9, 1024), (18, 11, 1024),
                                              (20, 11, 1024), (20, 12, 1024), (21, 12, 256),
-                                             (22, 11, 1024)])
+                                             (21, 12, 32), (22, 11, 1024), (22, 11, 64)])
 def test_four_step_splits_against_oracle(bps, ctx, orc, logn, log_cols, W):
     """Other four-step splits N/2 = R x C (other radix structures of both FFT passes;
     where a pass-2 CTA holds one or two row pairs and W <= R -- 2^21 with C = 4096, 2^22
