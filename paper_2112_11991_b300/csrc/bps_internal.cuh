@@ -36,6 +36,12 @@ struct __align__(16) Anchor {
 static_assert(sizeof(Anchor) == 64, "Anchor must be 64 bytes");
 
 // Problem geometry of one search (host-built, passed by value to kernels).
+// Row-major power layout of pass 2 (plan.ptrans): columns k2 in blocks of 2^kLogPowCols,
+// rows k1 in groups of NP; bin k1 + R k2 at
+//   P'[(k2 div 8) 8 R + (k1 div NP) 8 NP + (k2 mod 8) NP + k1 mod NP]
+// so the 8 columns x W rows of whitening blocks the median kernel takes are contiguous.
+constexpr int kLogPowCols = 3;
+
 struct Plan {
     int64_t n;      // real samples N (power of two)
     int64_t M;      // N/2 complex points of the packed FFT

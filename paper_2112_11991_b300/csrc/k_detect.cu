@@ -209,16 +209,17 @@ __global__ void __launch_bounds__(256, 4) k_median_warp(float* __restrict__ P, P
     if (lane == 0) scale[(int64_t)tl * nblk + blk] = sc;
 }
 
-// The same from pass 2's row-major power in groups of T = NP = 2^LOGT rows (bin k1 + R k2 at
-// Pt[(k1 div T) T C + k2 T + k1 mod T], W <= R, T <= W): a CTA of kMedCols warps takes
-// the kMedCols blocks at k2 in [k20, k20 + kMedCols), k1 in [q0, q0 + W) -- W/T runs of
-// 4 kMedCols T bytes -- into a shared tile padded to kMedCols + 1 words per row
-// (conflict-free column reads); warp w takes the median of column k20 + w and writes its
-// whitened block to P in bin order.  (Measured with T = 1 at C = 2048 and 4096: 32-byte
-// runs with four CTAs per SM beat 64-byte runs with two, whose 16 warps need more than
-// 64 registers with the candidate gather of the median.)
+// The same from pass 2's row-major power (kLogPowCols: columns in blocks of 8, rows in
+// groups of T = NP = 2^LOGT, W <= R, T <= W): a CTA of kMedCols = 8 warps takes the 8
+// blocks at k2 in [k20, k20 + 8), k1 in [q0, q0 + W) -- one contiguous run of 32 W bytes
+// -- into a shared tile padded to kMedCols + 1 words per row (conflict-free column
+// reads); warp w takes the median of column k20 + w and writes its whitened block to P in
+// bin order.  (Measured at C = 2048 and 4096: 8 columns with four CTAs per SM beat 16 with
+// two, whose 16 warps need more than 64 registers with the candidate gather of the
+// median.)
 constexpr int kMedCols = 8;
 constexpr int kLogMedCols = 3;
+static_assert(kLogMedCols == kLogPowCols, "the median CTA takes one column block");
 
 template <int VPL, int LOGT>
 __global__ void __launch_bounds__(32 * kMedCols) k_median_warp_t(const float* __restrict__ Pt, Plan p,
@@ -238,13 +239,13 @@ __global__ void __launch_bounds__(32 * kMedCols) k_median_warp_t(const float* __
     const int q0 = qb * W;
     const float* src = Pt + (int64_t)tl * p.M;
     constexpr int LCH = kLogMedCols + LOGT;  // log2 of the floats of one group's kMedCols columns
-    const float* g0 = src + ((int64_t)(q0 >> LOGT) << (LOGT + p.logC)) + ((int64_t)k20 << LOGT);
+    const float* g0 = src + ((int64_t)(k20 >> kLogMedCols) << (p.logR + kLogMedCols)) +
+                      ((int64_t)(q0 >> LOGT) << LCH);
 #pragma unroll 4
     for (int i = threadIdx.x; i < (W * kMedCols) / 4; i += 32 * kMedCols) {
         const int f = 4 * i;
         const int gi = f >> LCH, o = f & ((1 << LCH) - 1);
-        const float4 v =
-            __ldg(reinterpret_cast<const float4*>(g0 + ((int64_t)gi << (LOGT + p.logC)) + o));
+        const float4 v = __ldg(reinterpret_cast<const float4*>(g0 + f));
         const float e[4] = {v.x, v.y, v.z, v.w};
 #pragma unroll
         for (int u = 0; u < 4; ++u) {

@@ -470,14 +470,16 @@ __global__ void __launch_bounds__(1024, 1) k_pass2(const float2* __restrict__ Y,
     }
     float* Pt = P + (int64_t)tl * M;
     if (p.ptrans) {
-        // row-major power in groups of NP rows, column-major inside a group: bin k1 + R k2
-        // at P'[(k1 div NP) NP C + k2 NP + k1 mod NP], so this CTA's low rows are one
-        // contiguous NP C run (their mirrors straddle two groups).  Items q-fastest: a
-        // warp's low-row stores fill whole lines; the median kernel reads 8 columns of a
-        // group as one 32 NP-byte run.
+        // row-major power, columns in blocks of 8, rows in groups of NP (kLogPowCols):
+        // bin k1 + R k2 at P'[(k2 div 8) 8 R + (k1 div NP) 8 NP + (k2 mod 8) NP + k1 mod NP].
+        // Items q-fastest: a warp's low-row stores are 32 NP-byte runs of whole sectors
+        // (their mirrors straddle two groups), and the median kernel reads the 8 columns
+        // x W rows of its blocks as one contiguous run.
+        constexpr int LB = kLogPowCols;
         const int twsh = 12 - logC;
         const auto at_ = [&](int k1, int k2) -> int64_t {
-            return ((int64_t)(k1 >> logNP) << (logNP + logC)) + ((int64_t)k2 << logNP) +
+            return ((int64_t)(k2 >> LB) << (logR + LB)) +
+                   ((int64_t)(k1 >> logNP) << (logNP + LB)) + ((k2 & ((1 << LB) - 1)) << logNP) +
                    (k1 & (NP - 1));
         };
         static_assert(kEPT2 % 2 == 0, "items per thread");
