@@ -138,19 +138,31 @@ int bps_series_update(bps_ctx* ctx, int64_t series_id, const void* data, int on_
 int bps_load_bank(bps_ctx* ctx, const bps_template* t, int64_t count, int64_t* bank_id);
 
 /* Enqueue the search of every template of a bank over a series on
- * `cuda_stream` (a cudaStream_t; NULL = the context's own stream).  Returns at
- * once; *req_id receives a request id.  Workspace is allocated stream-ordered
- * and freed when the request completes. */
+ * `cuda_stream` (a cudaStream_t; NULL = the context's own stream): Algorithm 1's
+ * outer loop over the K templates, each template resampled, FFT'd (Sec. 2.4),
+ * whitened ("Fourier de-reddening", App. A), harmonic-summed (Sec. 2.1, S_L) and
+ * thresholded (Sec. 2.1, false-alarm statistics) as described at the top of
+ * this file.  Returns at once; *req_id receives a request id.
+ *   params      search parameters (see bps_search_params); checked before any
+ *               work is enqueued (BPS_ERR_INVALID_ARG, BPS_ERR_UNSUPPORTED when
+ *               an orbit is too fast for the FP32 index map)
+ * Workspace is allocated stream-ordered and freed when the request completes;
+ * the candidate buffer (params->cand_cap records) and its counters come from a
+ * pool owned by the context and return to it when the request is unloaded. */
 int bps_search(bps_ctx* ctx, int64_t series_id, int64_t bank_id,
                const bps_search_params* params, void* cuda_stream, int64_t* req_id);
 
 /* Non-blocking completion test: *done = 1 when the request has finished. */
 int bps_query(bps_ctx* ctx, int64_t req_id, int* done);
 
-/* Wait for a request and copy its candidates, sorted by (template_idx, nharm,
- * bin), into out[0 .. cap).  *n_written = candidates copied, *n_total = all
- * candidates found.  Returns BPS_ERR_CAND_OVERFLOW when the device capacity
- * (cand_cap) was exceeded: then the kept subset is arbitrary. */
+/* Wait for a request and copy its candidates -- the peak-detection output of
+ * App. A: every (template, harmonic level n, bin k) with S_n[k] >= thr_n
+ * (Sec. 2.1) -- sorted by (template_idx, nharm, bin), into out[0 .. cap)
+ * (host memory of the caller; out may be NULL with cap = 0 to query the count).
+ * *n_written = candidates copied, *n_total = all candidates found.  Returns
+ * BPS_ERR_CAND_OVERFLOW when the device capacity (cand_cap) was exceeded: then
+ * the kept subset is arbitrary; BPS_ERR_TIMEOUT when a bounded device wait
+ * expired (results incomplete). */
 int bps_fetch_candidates(bps_ctx* ctx, int64_t req_id, bps_candidate* out,
                          int64_t cap, int64_t* n_written, int64_t* n_total);
 
@@ -401,10 +413,16 @@ const char* bps_server_last_error(bps_server* srv);
  *   cuda_stream  cudaStream_t to run on (NULL = legacy default stream)
  * Returns BPS_OK, BPS_ERR_INVALID_ARG, BPS_ERR_UNSUPPORTED or BPS_ERR_CUDA;
  * the work is enqueued on the stream and the call does not wait for it.
+ * Results agree with bps_whitened_spectrum within the power tolerance, not bit
+ * for bit: the FP64 anchor block is chosen from this template alone
+ * (bps_whitened_spectrum chooses it from the whole bank), and an offset within
+ * rounding distance of a half-integer can round the other way with another block.
  * The scratch array is shared by every call and keeps the last call's
  * contents; calls that overlap on the GPU race on it and must be serialised.
- * The first call on a device looks up the array's address (cudaGetSymbolAddress,
- * with that device current); make that first call before any stream capture. */
+ * Each call whose stream is not being captured looks up the array's address
+ * (cudaGetSymbolAddress, with the current device; it allocates nothing); a call
+ * during a stream capture reuses the last address looked up on that device, so
+ * make one call on the device before any stream capture. */
 int bps_whitened_spectrum_noalloc(const float* d_series, int64_t n, double tsamp_s,
                                   double fill, const bps_template* tmpl,
                                   int32_t whiten_block, float* d_pw_out,

@@ -579,150 +579,15 @@ class Server:
         return {"queued": q.value, "active": a.value, "finished": f.value, "bytes_held": by.value}
 
 
-def bps_default_params(p):
-    return lib().bps_default_params(p)
-
-
-def bps_create(out, device):
-    return lib().bps_create(out, device)
-
-
-def bps_destroy(ctx):
-    return lib().bps_destroy(ctx)
-
-
-def bps_load_series(ctx, data, n, tsamp, dtype, on_device, sid):
-    return lib().bps_load_series(ctx, data, n, tsamp, dtype, on_device, sid)
-
-
-def bps_load_bank(ctx, t, count, bid):
-    return lib().bps_load_bank(ctx, t, count, bid)
-
-
-def bps_search(ctx, sid, bid, params, stream, rid):
-    return lib().bps_search(ctx, sid, bid, params, stream, rid)
-
-
-def bps_query(ctx, rid, done):
-    return lib().bps_query(ctx, rid, done)
-
-
-def bps_fetch_candidates(ctx, rid, out, cap, nw, nt):
-    return lib().bps_fetch_candidates(ctx, rid, out, cap, nw, nt)
-
-
-def bps_unload(ctx, id_):
-    return lib().bps_unload(ctx, id_)
-
-
-def bps_last_error(ctx):
-    return lib().bps_last_error(ctx)
-
-
-def bps_index_map(ctx, sid, bid, t, out, npre):
-    return lib().bps_index_map(ctx, sid, bid, t, out, npre)
-
-
-def bps_whitened_spectrum(ctx, sid, bid, t0, count, params, out):
-    return lib().bps_whitened_spectrum(ctx, sid, bid, t0, count, params, out)
-
-
-def bps_harmonic_sums(ctx, sid, bid, t, params, out):
-    return lib().bps_harmonic_sums(ctx, sid, bid, t, params, out)
-
-
-def bps_thresholds(params, n, k, out):
-    return lib().bps_thresholds(params, n, k, out)
-
-
-def bps_whitened_spectrum_noalloc(d_series, n, tsamp, fill, tmpl, whiten_block, d_out, stream):
-    """Allocation-free whitened spectrum of one template (see include/bps.h)."""
-    return lib().bps_whitened_spectrum_noalloc(d_series, n, tsamp, fill, tmpl, whiten_block,
-                                               d_out, stream)
-
-
-def bps_server_create(ctx, cfg, out):
-    return lib().bps_server_create(ctx, cfg, out)
-
-
-def bps_server_destroy(srv):
-    return lib().bps_server_destroy(srv)
-
-
-def bps_server_submit(srv, series, n, tsamp, dtype, bank, count, params, ticket):
-    return lib().bps_server_submit(srv, series, n, tsamp, dtype, bank, count, params, ticket)
-
-
-def bps_server_result(srv, ticket, timeout_ms, out, cap, nw, nt, lat):
-    return lib().bps_server_result(srv, ticket, timeout_ms, out, cap, nw, nt, lat)
-
-
-def bps_server_stats(srv, q, a, f, by):
-    return lib().bps_server_stats(srv, q, a, f, by)
-
-
-def bps_server_last_error(srv):
-    return lib().bps_server_last_error(srv)
-
-
-def bps_autotune(ctx, sid, bid, base, sample, best, ms):
-    return lib().bps_autotune(ctx, sid, bid, base, sample, best, ms)
-
-
-def bps_distill(cin, n_in, n_samples, tsamp, tol, max_ratio, out, cap, n_out):
-    return lib().bps_distill(cin, n_in, n_samples, tsamp, tol, max_ratio, out, cap, n_out)
-
-
-def bps_set_profiling(ctx, on):
-    return lib().bps_set_profiling(ctx, on)
-
-
-def bps_selftest_bounded_wait(ctx, limit, timed_out):
-    return lib().bps_selftest_bounded_wait(ctx, limit, timed_out)
-
-
-def bps_whiten(ctx, d_power, count, nbins, whiten_block, d_pw_out, d_scale_out, stream):
-    return lib().bps_whiten(ctx, d_power, count, nbins, whiten_block, d_pw_out, d_scale_out,
-                            stream)
-
-
-def bps_default_bank_spec(spec):
-    return lib().bps_default_bank_spec(spec)
-
-
-def bps_metric_density(spec, t, count, out):
-    return lib().bps_metric_density(spec, t, count, out)
-
-
-def bps_metric_projected(spec, t, out):
-    return lib().bps_metric_projected(spec, t, out)
-
-
-def bps_metric_bank(spec, seed, out, cap, n_out, vol, nexp):
-    return lib().bps_metric_bank(spec, seed, out, cap, n_out, vol, nexp)
-
-
-def bps_series_update(ctx, sid, data, on_device):
-    return lib().bps_series_update(ctx, sid, data, on_device)
-
-
-def bps_graph_create(ctx, count, sids, bids, params, gid):
-    return lib().bps_graph_create(ctx, count, sids, bids, params, gid)
-
-
-def bps_graph_launch(ctx, gid, stream):
-    return lib().bps_graph_launch(ctx, gid, stream)
-
-
-def bps_graph_fetch(ctx, gid, pair, out, cap, nw, nt):
-    return lib().bps_graph_fetch(ctx, gid, pair, out, cap, nw, nt)
-
-
-def bps_request_stats(ctx, rid, out):
-    return lib().bps_request_stats(ctx, rid, out)
+def __getattr__(name):
+    """The C entry points under their own names (``bps.bps_search(...)`` and so on):
+    module attributes that resolve to the library's typed ctypes functions."""
+    if name in EXPORTED:
+        return getattr(lib(), name)
+    raise AttributeError("module %r has no attribute %r" % (__name__, name))
 
 
 __all__ = ["Context", "Server", "distill", "bps_server_config", "bps_bank_spec",
            "default_bank_spec", "metric_density", "metric_projected", "metric_bank", "BpsError", "default_params", "thresholds", "CAND_DTYPE", "EXPORTED",
-           "STAGES", "bps_template", "bps_candidate", "bps_search_params", "bps_stats"] + EXPORTED + [
+           "STAGES", "bps_template", "bps_candidate", "bps_search_params", "bps_stats"] + [
     n for n in dir() if n.startswith("BPS_")]

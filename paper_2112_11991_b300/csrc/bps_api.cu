@@ -70,11 +70,21 @@ try {
         return BPS_ERR_CUDA;
     bps_ctx* ctx = new bps_ctx();
     ctx->device = device;
-    if (cudaSetDevice(device) != cudaSuccess ||
+    cudaMemPoolProps pp;
+    std::memset(&pp, 0, sizeof pp);
+    pp.allocType = cudaMemAllocationTypePinned;
+    pp.location.type = cudaMemLocationTypeDevice;
+    pp.location.id = device;
+    uint64_t keep = UINT64_MAX;
+    if (cudaSetDevice(device) != cudaSuccess || cudaMemPoolCreate(&ctx->pool, &pp) != cudaSuccess ||
+        cudaMemPoolSetAttribute(ctx->pool, cudaMemPoolAttrReleaseThreshold, &keep) != cudaSuccess ||
         cudaStreamCreateWithFlags(&ctx->stream, cudaStreamNonBlocking) != cudaSuccess ||
         cudaMalloc((void**)&ctx->tw, kTwiddleN * sizeof(float2)) != cudaSuccess ||
         launch_twiddle_init(ctx->tw, ctx->stream) != cudaSuccess ||
         cudaStreamSynchronize(ctx->stream) != cudaSuccess) {
+        if (ctx->tw) cudaFree(ctx->tw);
+        if (ctx->stream) cudaStreamDestroy(ctx->stream);
+        if (ctx->pool) cudaMemPoolDestroy(ctx->pool);
         delete ctx;
         return BPS_ERR_CUDA;
     }
@@ -94,19 +104,19 @@ static void free_series(Series& s)
     s = Series();
 }
 
-static void free_request(Request& r)
+// Return a request's device buffers to the context's pool (after its work is done) and
+// its completion event to the free list.
+static void free_request(bps_ctx* ctx, Request& r)
 {
     for (auto& e : r.ev) {
         cudaEventDestroy(e.second.first);
         cudaEventDestroy(e.second.second);
     }
     r.ev.clear();
-    if (r.done) {
-        cudaEventSynchronize(r.done);
-        cudaEventDestroy(r.done);
-    }
-    if (r.d_cands) cudaFree(r.d_cands);
-    if (r.d_count) cudaFree(r.d_count);
+    if (r.done) cudaEventSynchronize(r.done);
+    if (r.d_cands) cudaFreeAsync(r.d_cands, ctx->stream);
+    if (r.d_count) cudaFreeAsync(r.d_count, ctx->stream);
+    event_put(ctx, r.done);
     r = Request();
 }
 
@@ -117,13 +127,18 @@ try {
         std::lock_guard<std::recursive_mutex> lk(ctx->mu);
         cudaSetDevice(ctx->device);
         cudaDeviceSynchronize();
-        for (auto& r : ctx->reqs) free_request(r.second);
+        for (auto& r : ctx->reqs) free_request(ctx, r.second);
         for (auto& s : ctx->series) free_series(s.second);
         for (auto& b : ctx->banks) cudaFree(b.second.d);
         for (auto& f : ctx->ffts) cufftDestroy(f.second);
         for (auto& gr : ctx->graphs) delete gr.second;
         if (ctx->tw) cudaFree(ctx->tw);
-        if (ctx->stream) cudaStreamDestroy(ctx->stream);
+        for (auto e : ctx->free_events) cudaEventDestroy(e);
+        if (ctx->stream) {
+            cudaStreamSynchronize(ctx->stream);
+            cudaStreamDestroy(ctx->stream);
+        }
+        if (ctx->pool) cudaMemPoolDestroy(ctx->pool);
     }
     delete ctx;
 } catch (...) {
@@ -205,7 +220,7 @@ try {
     } else if (on_device) {
         src = (float*)data;
     } else {
-        CK(cudaMallocAsync((void**)&src, bytes, st));
+        CK(pool_alloc(ctx, (void**)&src, bytes, st));
         CK(cudaMemcpyAsync(src, data, bytes, cudaMemcpyHostToDevice, st));
     }
     CK(cudaMemsetAsync(s.d_sum, 0, sizeof(double), st));
@@ -277,13 +292,16 @@ try {
     r.bank = bank_id;
     r.K = b->K;
     r.cap = params->cand_cap;
-    CK(cudaMalloc((void**)&r.d_cands, sizeof(Cand) * (size_t)r.cap));
-    CK(cudaMalloc((void**)&r.d_count, 2 * sizeof(unsigned long long)));  // count, status
+    // candidate buffer, counter + status word and completion event: stream-ordered from
+    // the context's pool and free list (no synchronous allocation per request)
+    CK(pool_alloc(ctx, (void**)&r.d_cands, sizeof(Cand) * (size_t)r.cap, st));
+    CK(pool_alloc(ctx, (void**)&r.d_count, 2 * sizeof(unsigned long long), st));
     CK(cudaMemsetAsync(r.d_count, 0, 2 * sizeof(unsigned long long), st));
-    CK(cudaEventCreateWithFlags(&r.done, cudaEventDisableTiming));
+    CK(event_get(ctx, &r.done));
     Job job;
     if ((rc = job.setup(ctx, s, b, *params, st, r.d_cands, r.d_count, r.cap))) {
-        free_request(r);
+        cudaStreamSynchronize(st);
+        free_request(ctx, r);
         return rc;
     }
     r.batch = job.nt;
@@ -295,7 +313,7 @@ try {
     job.release();
     if (rc) {
         cudaStreamSynchronize(st);
-        free_request(r);
+        free_request(ctx, r);
         return rc;
     }
     CK(cudaEventRecord(r.done, st));
@@ -348,7 +366,7 @@ try {
         if (kept) CK(cudaMemcpy(r.result.data(), r.d_cands, sizeof(Cand) * kept, cudaMemcpyDeviceToHost));
         sort_candidates(r.result);
         r.synced = true;
-        cudaFree(r.d_cands);
+        cudaFreeAsync(r.d_cands, ctx->stream);  // the request's work is done (synchronised)
         r.d_cands = nullptr;
     }
     const int64_t nw = std::min<int64_t>(cap, (int64_t)r.result.size());
@@ -394,7 +412,7 @@ try {
         return BPS_OK;
     }
     if (ctx->reqs.count(id)) {
-        free_request(ctx->reqs[id]);
+        free_request(ctx, ctx->reqs[id]);
         ctx->reqs.erase(id);
         return BPS_OK;
     }
@@ -700,9 +718,9 @@ try {
     Anchor* anc = nullptr;
     int32_t* idx = nullptr;
     unsigned long long* cnt = nullptr;
-    CK(cudaMallocAsync((void**)&anc, sizeof(Anchor) * p.nanchor, st));
-    CK(cudaMallocAsync((void**)&idx, sizeof(int32_t) * p.n, st));
-    CK(cudaMallocAsync((void**)&cnt, sizeof(unsigned long long), st));
+    CK(pool_alloc(ctx, (void**)&anc, sizeof(Anchor) * p.nanchor, st));
+    CK(pool_alloc(ctx, (void**)&idx, sizeof(int32_t) * p.n, st));
+    CK(pool_alloc(ctx, (void**)&cnt, sizeof(unsigned long long), st));
     CK(cudaMemsetAsync(cnt, 0, sizeof(unsigned long long), st));
     CK(launch_anchors(b->d, template_idx, 1, p, anc, st));
     CK(launch_index_map(anc, p, idx, cnt, st));
@@ -739,7 +757,7 @@ try {
     const int nt = (int)count;
     if ((rc = ws_alloc(ctx, p, nt, params->mode, st, w))) return rc;
     float* out = nullptr;
-    CK(cudaMallocAsync((void**)&out, sizeof(float) * p.M * nt, st));
+    CK(pool_alloc(ctx, (void**)&out, sizeof(float) * p.M * nt, st));
     StageTimer tm;
     if ((rc = run_spectrum(ctx, *s, *b, p, params->mode, t0, nt, w, st, tm))) return rc;
     CK(launch_whitened(w.P, w.scale, nt, p, out, st));
@@ -773,9 +791,9 @@ try {
     float* so = nullptr;
     Cand* cd = nullptr;
     unsigned long long* cnt = nullptr;
-    CK(cudaMallocAsync((void**)&so, sizeof(float) * p.M * p.nlev, st));
-    CK(cudaMallocAsync((void**)&cd, sizeof(Cand), st));
-    CK(cudaMallocAsync((void**)&cnt, 2 * sizeof(unsigned long long), st));
+    CK(pool_alloc(ctx, (void**)&so, sizeof(float) * p.M * p.nlev, st));
+    CK(pool_alloc(ctx, (void**)&cd, sizeof(Cand), st));
+    CK(pool_alloc(ctx, (void**)&cnt, 2 * sizeof(unsigned long long), st));
     CK(cudaMemsetAsync(cnt, 0, 2 * sizeof(unsigned long long), st));
     StageTimer tm;
     if ((rc = run_spectrum(ctx, *s, *b, p, params->mode, template_idx, 1, w, st, tm))) return rc;

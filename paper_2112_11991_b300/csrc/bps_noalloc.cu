@@ -17,9 +17,16 @@
 //     each call overwrites every byte it reads, so nothing needs clearing;
 //   * calls whose work overlaps on the GPU (different streams, or different
 //     host threads) race on the array: serialise them;
-//   * the first call on a device looks up the array's device address with
-//     cudaGetSymbolAddress (with that device current); make that first call
-//     before any stream capture.
+//   * every call made while its stream is not being captured looks up the array's
+//     device address with cudaGetSymbolAddress (with the call's device current; the
+//     lookup allocates nothing), so a context torn down and re-created in between
+//     (cudaDeviceReset) is followed; a call made during a stream capture uses the
+//     address of the last uncaptured call on that device, so make one call before
+//     any capture;
+//   * the anchor block is chosen from this one template's orbit (bps_whitened_spectrum
+//     chooses it from the whole bank), so results agree with bps_whitened_spectrum
+//     within the power tolerance of the parity tests, not bit for bit: near-half-
+//     integer offsets can round the other way with another anchor block.
 #include <cmath>
 #include <mutex>
 
@@ -40,27 +47,34 @@ std::mutex g_mu;
 unsigned char* g_scratch_dev[kMaxDevices] = {};
 
 // Device address of g_scratch on the current device (host code may not use the
-// symbol itself: on the host it names a stand-in, not device memory).
-int scratch_address(unsigned char** out)
+// symbol itself: on the host it names a stand-in, not device memory).  Looked up
+// afresh unless the stream is being captured (then the last address looked up on
+// this device is used; none yet is an error).
+int scratch_address(cudaStream_t st, unsigned char** out)
 {
     int dev = 0;
     if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= kMaxDevices) return BPS_ERR_CUDA;
+    cudaStreamCaptureStatus cs = cudaStreamCaptureStatusNone;
+    if (cudaStreamIsCapturing(st, &cs) != cudaSuccess) return BPS_ERR_CUDA;
     std::lock_guard<std::mutex> lk(g_mu);
-    if (!g_scratch_dev[dev]) {
+    if (cs == cudaStreamCaptureStatusNone) {
         void* p = nullptr;
         if (cudaGetSymbolAddress(&p, g_scratch) != cudaSuccess || !p) return BPS_ERR_CUDA;
         g_scratch_dev[dev] = (unsigned char*)p;
     }
+    if (!g_scratch_dev[dev]) return BPS_ERR_CUDA;
     *out = g_scratch_dev[dev];
     return BPS_OK;
 }
 
 __global__ void k_store_template(DevTemplate t, DevTemplate* dst) { *dst = t; }
 
+// log2 of v when v is a power of two in [1, 2^62], else -1 (no shift past bit 62)
 int ilog2_exact(int64_t v)
 {
+    if (v < 1 || v > (1ll << 62)) return -1;
     int l = 0;
-    while ((1ll << l) < v) ++l;
+    while (l < 62 && (1ll << l) < v) ++l;
     return (1ll << l) == v ? l : -1;
 }
 
@@ -78,6 +92,7 @@ extern "C" int bps_whitened_spectrum_noalloc(const float* d_series, int64_t n, d
                                              void* cuda_stream)
 try {
     if (!d_series || !tmpl || !d_pw_out) return BPS_ERR_INVALID_ARG;
+    if (n > (1ll << kMaxLogN) && ilog2_exact(n) > 0) return BPS_ERR_UNSUPPORTED;
     const int logn = ilog2_exact(n);
     if (logn < 11) return BPS_ERR_INVALID_ARG;
     if (logn > kMaxLogN) return BPS_ERR_UNSUPPORTED;  // beyond the fixed scratch array
@@ -118,8 +133,9 @@ try {
     const size_t a_p = up256(sizeof(float) * (size_t)p.M);
     const size_t a_sc = up256(sizeof(float) * (size_t)(p.M >> p.logW));
     if (a_tw + a_tm + a_an + a_y + a_p + a_sc > kScratchBytes) return BPS_ERR_UNSUPPORTED;
+    cudaStream_t st = (cudaStream_t)cuda_stream;
     unsigned char* base = nullptr;
-    int rc = scratch_address(&base);
+    int rc = scratch_address(st, &base);
     if (rc) return rc;
     float2* tw = (float2*)base;
     DevTemplate* dt = (DevTemplate*)(base + a_tw);
@@ -128,7 +144,6 @@ try {
     float* P = (float*)(base + a_tw + a_tm + a_an + a_y);
     float* scale = (float*)(base + a_tw + a_tm + a_an + a_y + a_p);
 
-    cudaStream_t st = (cudaStream_t)cuda_stream;
     DevTemplate tv;
     tv.porb = t.porb_s;
     tv.tau = t.tau_lts;

@@ -74,6 +74,11 @@ struct GraphObj;
 struct bps_ctx {
     int device = 0;
     cudaStream_t stream = nullptr;
+    // stream-ordered device memory of workspaces and candidate buffers: a pool of the
+    // context that keeps what is freed (release threshold: never), so after the first
+    // request of a size no allocation reaches the driver
+    cudaMemPool_t pool = nullptr;
+    std::vector<cudaEvent_t> free_events;  // completion events for reuse
     std::recursive_mutex mu;
     std::string err = "";
     int64_t next_id = 1;
@@ -319,11 +324,33 @@ inline size_t ws_carve(const Plan& p, int nt, int mode, int anchor_templates, ch
     return a + y + x + pp + pt + sc;
 }
 
+// Stream-ordered allocation from the context's pool.
+inline cudaError_t pool_alloc(bps_ctx* ctx, void** p, size_t bytes, cudaStream_t st)
+{
+    return cudaMallocFromPoolAsync(p, bytes, ctx->pool, st);
+}
+
+// A completion event from the context's free list (created when the list is empty).
+inline cudaError_t event_get(bps_ctx* ctx, cudaEvent_t* e)
+{
+    if (!ctx->free_events.empty()) {
+        *e = ctx->free_events.back();
+        ctx->free_events.pop_back();
+        return cudaSuccess;
+    }
+    return cudaEventCreateWithFlags(e, cudaEventDisableTiming);
+}
+
+inline void event_put(bps_ctx* ctx, cudaEvent_t e)
+{
+    if (e) ctx->free_events.push_back(e);
+}
+
 inline int ws_alloc(bps_ctx* ctx, const Plan& p, int nt, int mode, cudaStream_t st, Workspace& w,
              int anchor_templates = 0)
 {
     char* base = nullptr;
-    CK(cudaMallocAsync((void**)&base, ws_carve(p, nt, mode, anchor_templates, nullptr, nullptr), st));
+    CK(pool_alloc(ctx, (void**)&base, ws_carve(p, nt, mode, anchor_templates, nullptr, nullptr), st));
     ws_carve(p, nt, mode, anchor_templates, base, &w);
     return BPS_OK;
 }

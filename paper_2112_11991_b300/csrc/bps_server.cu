@@ -172,18 +172,18 @@ bool admit_one(bps_server* srv, SReq& q, int slot)
     q.b.h = q.bank;
     float* src = nullptr;
     if (q.dtype == BPS_F32) {
-        chk(cudaMallocAsync((void**)&q.s.f32, 4 * n, st));
+        chk(pool_alloc(srv->ctx, (void**)&q.s.f32, 4 * n, st));
         src = q.s.f32;
     } else {
-        chk(cudaMallocAsync((void**)&q.d_stage, 4 * n, st));
-        chk(cudaMallocAsync((void**)&q.s.f16, 2 * n, st));
-        chk(cudaMallocAsync((void**)&q.s.scale, 4 * (((n + 4095) >> 12) + 1), st));
+        chk(pool_alloc(srv->ctx, (void**)&q.d_stage, 4 * n, st));
+        chk(pool_alloc(srv->ctx, (void**)&q.s.f16, 2 * n, st));
+        chk(pool_alloc(srv->ctx, (void**)&q.s.scale, 4 * (((n + 4095) >> 12) + 1), st));
         src = q.d_stage;
     }
-    chk(cudaMallocAsync((void**)&q.d_sum, sizeof(double), st));
-    chk(cudaMallocAsync((void**)&q.b.d, sizeof(DevTemplate) * q.bank.size(), st));
-    chk(cudaMallocAsync((void**)&q.d_cands, sizeof(Cand) * (size_t)q.prm.cand_cap, st));
-    chk(cudaMallocAsync((void**)&q.d_count, 2 * sizeof(unsigned long long), st));
+    chk(pool_alloc(srv->ctx, (void**)&q.d_sum, sizeof(double), st));
+    chk(pool_alloc(srv->ctx, (void**)&q.b.d, sizeof(DevTemplate) * q.bank.size(), st));
+    chk(pool_alloc(srv->ctx, (void**)&q.d_cands, sizeof(Cand) * (size_t)q.prm.cand_cap, st));
+    chk(pool_alloc(srv->ctx, (void**)&q.d_count, 2 * sizeof(unsigned long long), st));
     if (ok) {
         chk(cudaMemcpyAsync(src, q.h_series, 4 * n, cudaMemcpyHostToDevice, st));
         chk(cudaMemcpyAsync(q.b.d, q.bank.data(), sizeof(DevTemplate) * q.bank.size(),

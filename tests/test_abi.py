@@ -88,3 +88,15 @@ def test_oracle_not_imported_by_package():
         for f in files:
             if f.endswith((".py", ".cu", ".cuh", ".h", ".cpp")):
                 assert not pat.search(open(os.path.join(dirpath, f)).read()), f
+
+
+def test_c_names_resolve_to_library_functions(bps):
+    """The binding offers every entry point under its C name (argument marshalling only)."""
+    L = bps.lib()
+    for n in bps.EXPORTED:
+        assert getattr(bps, n) is getattr(L, n), n
+    p = bps.bps_search_params()
+    bps.bps_default_params(C.byref(p))
+    assert p.nharm_max == 16
+    with pytest.raises(AttributeError):
+        bps.bps_no_such_call

@@ -3,8 +3,11 @@
 * HTRU-like circular search, 2^23 samples x 4096 templates (the benchmark
   workload, default batch and tiles): the whole bank is searched on the GPU and
   a sample of templates (the three true orbits and two random ones) is checked
-  against the FP64 oracle, candidate by candidate; each injected pulsar is
-  found under its true orbit at round(n T / P) for some harmonic level n.
+  against the FP64 oracle, candidate by candidate, on the GPU's validated index
+  maps; the three true orbits are also checked end to end, against the oracle on
+  its own index maps (samples rounded differently counted, the power and
+  candidate deviations they allow bounded); each injected pulsar is found under
+  its true orbit at round(n T / P) for some harmonic level n.
 * 2^24 samples (8192-point column FFTs): whitened spectrum of one template.
 * 2^25 samples, the largest size (elliptical IMBH workload shape): whitened
   spectrum and candidates of the two true orbits and one random template; the same
@@ -15,7 +18,7 @@ import numpy as np
 import pytest
 
 import synth
-from gpu_common import PW_TOL, compare_candidates, oracle_on_gpu_maps, pw_close
+from gpu_common import PW_TOL, compare_candidates, end_to_end_leg, oracle_on_gpu_maps, pw_close
 
 pytestmark = pytest.mark.gpu
 
@@ -71,11 +74,19 @@ def test_htru_2p23_full_bank_sampled(bps, ctx, orc):
     sample = list(w.true_idx) + others
     sub = w.bank[sample]
     sbid = ctx.load_bank(sub)
-    oc, _ = oracle_on_gpu_maps(ctx, orc, sid, sbid, w.series, w.tsamp, sub)
+    oc, res = oracle_on_gpu_maps(ctx, orc, sid, sbid, w.series, w.tsamp, sub)
     # relabel the oracle's template indices (0..4 in the sub-bank) to bank indices
     oc["template_idx"] = np.array(sample)[oc["template_idx"]]
     g_sub = gc[np.isin(gc["template_idx"], sample)]
-    compare_candidates(g_sub, oc, thr)
+    matched, excused = compare_candidates(g_sub, oc, thr)
+    print("\n[parity] 2^23 GPU-map leg: %d candidates matched, %d excused at the threshold"
+          % (matched, excused))
+    # end to end: the oracle on its own index map for the three true orbits
+    for i, ti in enumerate(w.true_idx):
+        pw = ctx.whitened_spectrum(sid, bid, int(ti), 1, w.n, prm)[0]
+        r = end_to_end_leg(orc, w.series, w.tsamp, w.bank[ti], res[i]["idx_gpu"], pw,
+                           gc[gc["template_idx"] == ti], thr)
+        print("[parity] 2^23 end-to-end leg, template %d: %s" % (ti, r))
     T = w.n * w.tsamp
     for ti, p in zip(w.true_idx, w.pulsars):
         assert _recovered(gc[gc["template_idx"] == ti], T, p.period_s, thr), ti

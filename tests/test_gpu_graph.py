@@ -4,6 +4,9 @@ updates (bps_series_update).
 * a graph over pairs of different series lengths, banks (circular and eccentric) and
   storage types returns, per pair, exactly the candidates of a plain bps_search of
   the same pair; a second replay returns them again;
+* per pair, the graph's candidates of the true orbit and one other template agree with
+  the FP64 oracle (on the GPU's validated index maps; FP16 pairs against the oracle on
+  the FP32 series at the FP16 tolerance);
 * after bps_series_update of one series, a replay of the same graph returns the
   candidates of a fresh search of the new data (the other pairs unchanged);
 * the plain form cannot be captured; a series or bank captured in a graph cannot be
@@ -13,6 +16,7 @@ import numpy as np
 import pytest
 
 import synth
+from gpu_common import F16_TOL, PW_TOL, compare_candidates, oracle_subset
 
 pytestmark = pytest.mark.gpu
 
@@ -41,17 +45,17 @@ def _pair(bps, ctx, logn, K, ecc, f16, seed):
     p = synth.Pulsar(period_s=0.025, porb_s=4 * T, tau_lts=0.05, phi_rad=1.0 + seed,
                      omega_rad=0.5 if ecc else 0.0, ecc=0.05 if ecc else 0.0, amp=0.3)
     x = synth.inject(synth.noise(n, 700 + seed), ts, p)
-    bank, _ = synth.uniform_bank(K, 800 + seed, (3 * T, 10 * T), (0.0, 0.1),
-                                 ecc=(0.0, 0.1) if ecc else None, true_orbits=[p.orbit()])
+    bank, where = synth.uniform_bank(K, 800 + seed, (3 * T, 10 * T), (0.0, 0.1),
+                                     ecc=(0.0, 0.1) if ecc else None, true_orbits=[p.orbit()])
     dt = bps.BPS_F16_SCALED if f16 else bps.BPS_F32
-    return ctx.load_series(x, ts, dt), ctx.load_bank(bank), x, ts, bank, dt
+    return ctx.load_series(x, ts, dt), ctx.load_bank(bank), x, ts, bank, dt, int(where[0])
 
 
 SHAPES = [(16, 24, False, False), (18, 40, True, False), (20, 12, False, True),
           (17, 64, True, False), (19, 8, False, False), (16, 5, True, False)]
 
 
-def test_graph_matches_search_and_update(bps, ctx):
+def test_graph_matches_search_and_update(bps, ctx, orc):
     import torch
     prm = bps.default_params(sigma_thr=5.0)
     pairs = [_pair(bps, ctx, *s, seed=i) for i, s in enumerate(SHAPES)]
@@ -65,9 +69,17 @@ def test_graph_matches_search_and_update(bps, ctx):
             assert tot == c.size
             assert np.array_equal(c, ref[i]), (rep, i)
     assert sum(r.size for r in ref) > 0
+    # the graph's candidates against the FP64 oracle on two templates per pair
+    for i, (sid, bid, x, ts, bank, dt, ti) in enumerate(pairs):
+        c, _ = ctx.graph_fetch(gid, i)
+        sample = sorted({ti, (ti + 1) % len(bank)})
+        oc, _ = oracle_subset(ctx, orc, sid, x, ts, bank, sample, sigma=5.0)
+        tol = F16_TOL if dt == bps.BPS_F16_SCALED else PW_TOL
+        compare_candidates(c[np.isin(c["template_idx"], sample)], oc,
+                           bps.thresholds(prm, x.size, len(bank)), tol=tol)
     # new data for pairs 1 (FP32) and 2 (FP16): the same graph searches it
     for j in (1, 2):
-        sid, bid, x, ts, bank, dt = pairs[j]
+        sid, bid, x, ts, bank, dt, _ = pairs[j]
         x2 = synth.noise(x.size, 900 + j) + np.float32(0.5) * np.sin(
             2 * np.pi * np.arange(x.size) * ts / 0.013).astype(np.float32)
         ctx.update_series(sid, x2 if j == 1 else torch.from_numpy(x2).cuda())

@@ -3,6 +3,9 @@
 * every request's candidates are identical whether it runs alone or mixed with
   requests of other series lengths, banks and storage types (and identical to a
   plain bps_search of the same inputs);
+* every request's candidates of its true orbit and one other template agree with the
+  FP64 oracle (on the GPU's validated index maps; the FP16 request against the oracle
+  on the FP32 series at the FP16 tolerance);
 * with an HBM budget that fits about one request, later requests wait in the queue
   and all complete; a request larger than the budget is refused at submission;
 * latencies are measured from submission to candidates on the host.
@@ -13,6 +16,7 @@ import numpy as np
 import pytest
 
 import synth
+from gpu_common import F16_TOL, PW_TOL, compare_candidates, oracle_subset
 
 pytestmark = pytest.mark.gpu
 
@@ -45,14 +49,15 @@ def _requests(bps):
         p = synth.Pulsar(period_s=0.025, porb_s=4 * T, tau_lts=0.05, phi_rad=1.0 + i,
                          omega_rad=0.5 if ecc else 0.0, ecc=0.05 if ecc else 0.0, amp=0.3)
         x = synth.inject(synth.noise(n, 300 + i), ts, p)
-        bank, _ = synth.uniform_bank(K, 400 + i, (3 * T, 10 * T), (0.0, 0.1),
-                                     ecc=(0.0, 0.1) if ecc else None, true_orbits=[p.orbit()])
-        out.append((x, ts, bank, bps.BPS_F16_SCALED if f16 else bps.BPS_F32))
+        bank, where = synth.uniform_bank(K, 400 + i, (3 * T, 10 * T), (0.0, 0.1),
+                                         ecc=(0.0, 0.1) if ecc else None, true_orbits=[p.orbit()])
+        out.append((x, ts, bank, bps.BPS_F16_SCALED if f16 else bps.BPS_F32, int(where[0])))
     return out
 
 
-def test_same_results_alone_and_in_the_mix(bps, ctx):
-    reqs = _requests(bps)
+def test_same_results_alone_and_in_the_mix(bps, ctx, orc):
+    reqs = [r[:4] for r in _requests(bps)]
+    truth = [r[4] for r in _requests(bps)]
     prm = bps.default_params(sigma_thr=5.0)
     with bps.Server(ctx, max_active=4, groups_in_flight=2) as srv:
         alone = []
@@ -66,6 +71,15 @@ def test_same_results_alone_and_in_the_mix(bps, ctx):
     for i in range(len(reqs)):
         assert np.array_equal(mixed[i], alone[i]), i
         assert np.array_equal(mixed[2 * len(reqs) - 1 - i], alone[i]), i
+    # served results against the FP64 oracle, two templates per request
+    for (x, ts, bank, dt), ti, c in zip(reqs, truth, alone):
+        sid = ctx.load_series(x, ts)
+        sample = sorted({ti, (ti + 1) % len(bank)})
+        oc, _ = oracle_subset(ctx, orc, sid, x, ts, bank, sample, sigma=5.0)
+        ctx.unload(sid)
+        tol = F16_TOL if dt == bps.BPS_F16_SCALED else PW_TOL
+        compare_candidates(c[np.isin(c["template_idx"], sample)], oc,
+                           bps.thresholds(prm, x.size, len(bank)), tol=tol)
     # the same kernels through the plain request path
     x, ts, bank, dt = reqs[1]
     sid = ctx.load_series(x, ts, dt)
@@ -76,7 +90,7 @@ def test_same_results_alone_and_in_the_mix(bps, ctx):
 
 
 def test_admission_queue_and_budget(bps, ctx):
-    reqs = _requests(bps)
+    reqs = [r[:4] for r in _requests(bps)]
     prm = bps.default_params(sigma_thr=5.0, cand_cap=1 << 16)
     x, ts, bank, dt = reqs[2]  # 2^20 samples: the largest request
     with bps.Server(ctx, max_active=4, groups_in_flight=2, hbm_budget=160 << 20) as srv:
@@ -96,7 +110,7 @@ def test_admission_queue_and_budget(bps, ctx):
 
 
 def test_nonblocking_result_and_invalid(bps, ctx):
-    reqs = _requests(bps)
+    reqs = [r[:4] for r in _requests(bps)]
     x, ts, bank, dt = reqs[0]
     with bps.Server(ctx, max_active=2) as srv:
         t = srv.submit(x, ts, bank, bps.default_params(), dt)
