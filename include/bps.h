@@ -351,8 +351,12 @@ int bps_autotune(bps_ctx* ctx, int64_t series_id, int64_t bank_id, const bps_sea
  * device as stream slots and HBM free up, and interleaves their launch groups (one
  * batch of templates each) round-robin, a few groups in flight per request, so a
  * request that arrives while others run starts within a launch group instead of
- * waiting for them to finish.  Each request's series and bank are copied to the
- * device at admission and freed when its candidates are on the host.  Results of a
+ * waiting for them to finish.  A request submitted with its own series
+ * (bps_server_submit) has its series and bank copied to the device at admission
+ * and freed when its candidates are on the host; a request on a resident series
+ * (bps_server_load_series + bps_server_submit_series) finds the series already on
+ * the device.  Device memory comes from the context's stream-ordered pool, which
+ * keeps freed blocks for later requests.  Results of a
  * request do not depend on what else runs (the per-template computation is the same
  * as bps_search's with the same parameters). */
 typedef struct bps_server bps_server;
@@ -378,6 +382,34 @@ void bps_server_destroy(bps_server* srv);
 int bps_server_submit(bps_server* srv, const float* series, int64_t n, double tsamp_s,
                       int dtype, const bps_template* bank, int64_t count,
                       const bps_search_params* params, int64_t* ticket);
+
+/* Load a series into the server's resident store (Algorithm 1's "dedispersed
+ * timeseries S sampled at t_samp", kept for many searches): the host data (n
+ * float32 samples, copied into pinned host memory before the call returns) is
+ * staged on the device by the first request that names it and stays there,
+ * counted against the HBM budget, for later requests.  When a request needs room,
+ * resident series that no queued or running request names are evicted, least
+ * recently used first; an evicted series is staged again from the host copy by
+ * the next request that names it.  Same sizes and dtypes as bps_load_series.
+ * *series_id receives the id (> 0) used by bps_server_submit_series.
+ * BPS_ERR_OUT_OF_MEMORY when the series alone exceeds the budget. */
+int bps_server_load_series(bps_server* srv, const float* series, int64_t n, double tsamp_s,
+                           int dtype, int64_t* series_id);
+
+/* Submit a search of `count` templates (host array, copied) over a resident series;
+ * the request pins the series (it is neither evicted nor unloadable) until its
+ * result is on the host.  Otherwise as bps_server_submit. */
+int bps_server_submit_series(bps_server* srv, int64_t series_id, const bps_template* bank,
+                             int64_t count, const bps_search_params* params, int64_t* ticket);
+
+/* Remove a series from the resident store (device copy and host copy).
+ * BPS_ERR_INVALID_ARG while unfinished requests name it, or for an unknown id. */
+int bps_server_unload_series(bps_server* srv, int64_t series_id);
+
+/* *resident = 1 while the series is on the device; *times_staged counts how often it
+ * was staged (1 + the times it was evicted and staged again).  Either may be NULL. */
+int bps_server_series_info(bps_server* srv, int64_t series_id, int32_t* resident,
+                           int64_t* times_staged);
 
 /* Wait up to timeout_ms (< 0: no limit) for a ticket; BPS_ERR_NOT_READY when it is
  * still running.  Then copies its sorted candidates like bps_fetch_candidates and

@@ -42,7 +42,8 @@ EXPORTED = ["bps_default_params", "bps_create", "bps_destroy", "bps_load_series"
             "bps_server_last_error", "bps_autotune", "bps_distill", "bps_series_update",
             "bps_graph_create", "bps_graph_launch", "bps_graph_fetch", "bps_default_bank_spec",
             "bps_metric_density", "bps_metric_projected", "bps_metric_bank",
-            "bps_selftest_bounded_wait", "bps_whiten"]
+            "bps_selftest_bounded_wait", "bps_whiten", "bps_server_load_series",
+            "bps_server_submit_series", "bps_server_unload_series", "bps_server_series_info"]
 STAGES = ["anchors", "pass1", "pass2", "power", "median", "harmsum"]
 
 
@@ -148,6 +149,14 @@ def lib():
         L.bps_server_result.restype = i32
         L.bps_server_result.argtypes = [vp, i64, C.c_int32, vp, i64, P(i64), P(i64),
                                         P(C.c_double)]
+        L.bps_server_load_series.restype = i32
+        L.bps_server_load_series.argtypes = [vp, vp, i64, C.c_double, i32, P(i64)]
+        L.bps_server_submit_series.restype = i32
+        L.bps_server_submit_series.argtypes = [vp, i64, vp, i64, P(bps_search_params), P(i64)]
+        L.bps_server_unload_series.restype = i32
+        L.bps_server_unload_series.argtypes = [vp, i64]
+        L.bps_server_series_info.restype = i32
+        L.bps_server_series_info.argtypes = [vp, i64, P(C.c_int32), P(i64)]
         L.bps_server_stats.restype = i32
         L.bps_server_stats.argtypes = [vp, P(i64), P(i64), P(i64), P(i64)]
         L.bps_server_last_error.restype = C.c_char_p
@@ -558,6 +567,34 @@ class Server:
                                      _np_ptr(b), b.shape[0], C.byref(params), C.byref(t))
         self._check(rc, "bps_server_submit")
         return t.value
+
+    def load_series(self, series, tsamp: float, dtype: int = BPS_F32) -> int:
+        """Put a series into the server's resident store; returns its server series id."""
+        x = np.ascontiguousarray(series, np.float32)
+        sid = C.c_int64()
+        self._check(lib().bps_server_load_series(self.h, _np_ptr(x), x.size, float(tsamp),
+                                                 int(dtype), C.byref(sid)),
+                    "bps_server_load_series")
+        return sid.value
+
+    def submit_series(self, series_id: int, bank, params: bps_search_params | None = None) -> int:
+        """Submit a search over a resident series; returns a ticket."""
+        params = params or default_params()
+        b = np.ascontiguousarray(np.asarray(bank, np.float64).reshape(-1, 5))
+        t = C.c_int64()
+        self._check(lib().bps_server_submit_series(self.h, int(series_id), _np_ptr(b), b.shape[0],
+                                                   C.byref(params), C.byref(t)),
+                    "bps_server_submit_series")
+        return t.value
+
+    def unload_series(self, series_id: int):
+        self._check(lib().bps_server_unload_series(self.h, int(series_id)), "bps_server_unload_series")
+
+    def series_info(self, series_id: int) -> dict:
+        r, n = C.c_int32(), C.c_int64()
+        self._check(lib().bps_server_series_info(self.h, int(series_id), C.byref(r), C.byref(n)),
+                    "bps_server_series_info")
+        return {"resident": bool(r.value), "times_staged": n.value}
 
     def result(self, ticket: int, timeout_ms: int = -1, allow_overflow=False):
         nw, nt, lat = C.c_int64(), C.c_int64(), C.c_double()

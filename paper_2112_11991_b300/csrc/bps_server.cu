@@ -13,6 +13,14 @@
 // on the device, then issues their launch groups round-robin (a few in flight per
 // request), and retires finished requests (candidates to the host, device memory
 // freed, slot released) so the next queued request can start.
+//
+// Resident series (bps_server_load_series): a series loaded into the server stays on
+// the device between requests that name it, counted against the HBM budget.  When a
+// request needs room, resident series that no queued or running request names are
+// evicted, least recently used first; the server keeps each series' pinned host copy,
+// so an evicted series is staged again by the next request that names it.
+// Device memory (series, banks, workspaces, candidates) comes from the context's
+// stream-ordered pool, which keeps freed blocks mapped for the next request.
 // =====================================================================================
 
 using namespace bps;
@@ -30,9 +38,12 @@ enum SState { S_QUEUED, S_STAGING, S_RUNNING, S_COUNTING, S_COPYING, S_DONE, S_F
 
 constexpr int64_t kPinnedCands = 1 << 16;  // candidates copied back through pinned memory
 
+struct SSeries;
+
 struct SReq {
     int64_t ticket = 0;
     SState state = S_QUEUED;
+    SSeries* ser = nullptr;     // resident series the request names (nullptr: its own copy)
     float* h_series = nullptr;  // pinned host copy of the submitted series
     int64_t n = 0;
     double tsamp = 0;
@@ -61,14 +72,43 @@ struct SReq {
     std::string err;
 };
 
-// Device bytes a request holds while resident (series + bank + workspace + candidates).
-size_t request_bytes(const Plan& p, int64_t K, const bps_search_params& prm, int dtype)
+// A series loaded into the server: pinned host copy (kept for re-staging) and, while
+// resident, its device storage.
+struct SSeries {
+    int64_t id = 0;
+    int64_t n = 0;
+    double tsamp = 0;
+    int dtype = BPS_F32;
+    float* h_series = nullptr;
+    double* h_sum = nullptr;
+    Series s;                  // device storage while resident (staging or staged)
+    float* d_stage = nullptr;  // FP32 staging buffer of an FP16 series while it is packed
+    double* d_sum = nullptr;
+    cudaEvent_t ready = nullptr;
+    bool resident = false, staging = false;
+    size_t bytes = 0;          // device bytes while resident (after packing)
+    size_t stage_bytes = 0;    // extra bytes while staging (the FP32 buffer of FP16 packing)
+    int refs = 0;              // queued and running requests naming it
+    int64_t times_staged = 0;
+    double last_use = 0;
+};
+
+// Device bytes of a series (FP32, or FP16 + scales) and of its FP32 staging buffer.
+size_t series_bytes(int64_t n, int dtype, size_t* staging)
+{
+    if (staging) *staging = dtype == BPS_F32 ? 0 : align256(4 * (size_t)n);
+    return dtype == BPS_F32 ? align256(4 * (size_t)n)
+                            : align256(2 * (size_t)n) + align256(4 * (size_t)(((n + 4095) >> 12) + 1));
+}
+
+// Device bytes a request holds while resident (bank + workspace + candidates, plus its
+// own series unless it names a resident one).
+size_t request_bytes(const Plan& p, int64_t K, const bps_search_params& prm, int dtype, bool own_series)
 {
     const int nt = prm.batch > 0 ? (int)std::min<int64_t>(prm.batch, K) : default_batch(p, K, prm.mode);
     const int64_t chunk = std::min<int64_t>((int64_t)nt * kAnchorChunk, K);
-    size_t ser = dtype == BPS_F32 ? align256(4 * (size_t)p.n)
-                                  : align256(2 * (size_t)p.n) + align256(4 * (size_t)((p.n + 4095) >> 12)) +
-                                        align256(4 * (size_t)p.n);  // FP32 staging while packing
+    size_t stg = 0;
+    const size_t ser = own_series ? series_bytes(p.n, dtype, &stg) + stg : 0;
     return ser + align256(sizeof(DevTemplate) * (size_t)K) + Job::workspace_bytes(p, nt, chunk, prm.mode) +
            align256(sizeof(Cand) * (size_t)prm.cand_cap) + 1024;
 }
@@ -83,6 +123,8 @@ struct bps_server {
     std::vector<char> busy;
     std::deque<int64_t> queue;
     std::map<int64_t, std::unique_ptr<SReq>> reqs;
+    std::map<int64_t, std::unique_ptr<SSeries>> series;  // resident-series store
+    int64_t next_series = 1;
     std::mutex mu;
     std::condition_variable cv;
     std::thread worker;
@@ -111,6 +153,11 @@ void release_device(SReq& q, cudaStream_t st)
         q.job->release();
         q.job.reset();
     }
+    if (q.ser) {  // the storage belongs to the resident series
+        q.s.f32 = nullptr;
+        q.s.f16 = nullptr;
+        q.s.scale = nullptr;
+    }
     if (q.s.f32) cudaFreeAsync(q.s.f32, st);
     if (q.s.f16) cudaFreeAsync(q.s.f16, st);
     if (q.s.scale) cudaFreeAsync(q.s.scale, st);
@@ -127,6 +174,16 @@ void release_device(SReq& q, cudaStream_t st)
     q.b.d = nullptr;
     q.d_cands = nullptr;
     q.d_count = nullptr;
+}
+
+void free_series_host(SSeries& ser)
+{
+    if (ser.h_series) cudaFreeHost(ser.h_series);
+    if (ser.h_sum) cudaFreeHost(ser.h_sum);
+    if (ser.ready) cudaEventDestroy(ser.ready);
+    ser.h_series = nullptr;
+    ser.h_sum = nullptr;
+    ser.ready = nullptr;
 }
 
 void release_host(SReq& q)
@@ -149,8 +206,82 @@ void release_host(SReq& q)
 
 namespace {
 
+// Stage a resident series on stream st: device storage from the pool, the host copy,
+// the FP64 sum (read back for the fill value) and FP16 packing; ser->ready marks the end.
+cudaError_t stage_series(bps_server* srv, SSeries& ser, cudaStream_t st)
+{
+    const size_t n = (size_t)ser.n;
+    cudaError_t e = cudaSuccess;
+    auto chk = [&](cudaError_t r) {
+        if (e == cudaSuccess) e = r;
+    };
+    ser.s = Series();
+    ser.s.n = ser.n;
+    ser.s.tsamp = ser.tsamp;
+    ser.s.dtype = ser.dtype;
+    ser.s.owned = true;
+    float* src = nullptr;
+    if (ser.dtype == BPS_F32) {
+        chk(pool_alloc(srv->ctx, (void**)&ser.s.f32, 4 * n, st));
+        src = ser.s.f32;
+    } else {
+        chk(pool_alloc(srv->ctx, (void**)&ser.d_stage, 4 * n, st));
+        chk(pool_alloc(srv->ctx, (void**)&ser.s.f16, 2 * n, st));
+        chk(pool_alloc(srv->ctx, (void**)&ser.s.scale, 4 * (((n + 4095) >> 12) + 1), st));
+        src = ser.d_stage;
+    }
+    chk(pool_alloc(srv->ctx, (void**)&ser.d_sum, sizeof(double), st));
+    if (e == cudaSuccess) {
+        chk(cudaMemcpyAsync(src, ser.h_series, 4 * n, cudaMemcpyHostToDevice, st));
+        chk(cudaMemsetAsync(ser.d_sum, 0, sizeof(double), st));
+        chk(launch_series_stats(src, ser.n, ser.d_sum, st));
+        if (ser.dtype != BPS_F32) chk(launch_f16_pack(src, ser.n, ser.s.f16, ser.s.scale, st));
+        chk(cudaMemcpyAsync(ser.h_sum, ser.d_sum, sizeof(double), cudaMemcpyDeviceToHost, st));
+        chk(cudaEventRecord(ser.ready, st));
+    }
+    ser.staging = true;
+    ser.times_staged += 1;
+    srv->used += ser.bytes + ser.stage_bytes;
+    return e;
+}
+
+// Free a resident series' device storage (no request names it, so none of its work is
+// in flight) and return its bytes to the budget.
+void evict_series(bps_server* srv, SSeries& ser)
+{
+    cudaStream_t st = srv->ctx->stream;
+    if (ser.s.f32) cudaFreeAsync(ser.s.f32, st);
+    if (ser.s.f16) cudaFreeAsync(ser.s.f16, st);
+    if (ser.s.scale) cudaFreeAsync(ser.s.scale, st);
+    if (ser.d_stage) cudaFreeAsync(ser.d_stage, st);
+    if (ser.d_sum) cudaFreeAsync(ser.d_sum, st);
+    ser.s = Series();
+    ser.d_stage = nullptr;
+    ser.d_sum = nullptr;
+    srv->used -= ser.bytes + (ser.staging ? ser.stage_bytes : 0);
+    ser.resident = ser.staging = false;
+}
+
+// Evict idle resident series, least recently used first, until `need` more bytes fit the
+// budget (or nothing idle is left); `keep` is never evicted.
+void make_room(bps_server* srv, size_t need, const SSeries* keep)
+{
+    while (srv->used + need > srv->budget) {
+        SSeries* lru = nullptr;
+        for (auto& kv : srv->series) {
+            SSeries& c = *kv.second;
+            if (&c == keep || c.refs > 0 || !(c.resident || c.staging)) continue;
+            if (!lru || c.last_use < lru->last_use) lru = &c;
+        }
+        if (!lru) return;
+        evict_series(srv, *lru);
+    }
+}
+
 // Stage a queued request onto a free slot: device buffers (stream-ordered), series and
-// bank copies, FP16 packing, the FP64 series sum read back for the fill value.
+// bank copies, FP16 packing, the FP64 series sum read back for the fill value.  A
+// request naming a resident series stages the series if it is not on the device and
+// then waits for it on its own stream.
 bool admit_one(bps_server* srv, SReq& q, int slot)
 {
     cudaStream_t st = srv->slots[slot];
@@ -170,6 +301,25 @@ bool admit_one(bps_server* srv, SReq& q, int slot)
     q.s.owned = true;
     q.b.K = (int64_t)q.bank.size();
     q.b.h = q.bank;
+    if (q.ser) {
+        SSeries& ser = *q.ser;
+        ser.last_use = now_s();
+        if (!ser.resident && !ser.staging) chk(stage_series(srv, ser, st));
+        if (ok) chk(cudaStreamWaitEvent(st, ser.ready, 0));
+        chk(pool_alloc(srv->ctx, (void**)&q.b.d, sizeof(DevTemplate) * q.bank.size(), st));
+        chk(pool_alloc(srv->ctx, (void**)&q.d_cands, sizeof(Cand) * (size_t)q.prm.cand_cap, st));
+        chk(pool_alloc(srv->ctx, (void**)&q.d_count, 2 * sizeof(unsigned long long), st));
+        if (ok) {
+            chk(cudaMemcpyAsync(q.b.d, q.bank.data(), sizeof(DevTemplate) * q.bank.size(),
+                                cudaMemcpyHostToDevice, st));
+            chk(cudaMemsetAsync(q.d_count, 0, 2 * sizeof(unsigned long long), st));
+            chk(cudaEventRecord(q.ev, st));
+        }
+        srv->busy[slot] = 1;
+        srv->used += q.bytes;
+        q.state = ok ? S_STAGING : S_FAILED;
+        return ok;
+    }
     float* src = nullptr;
     if (q.dtype == BPS_F32) {
         chk(pool_alloc(srv->ctx, (void**)&q.s.f32, 4 * n, st));
@@ -207,6 +357,10 @@ void finish(bps_server* srv, SReq& q, SState st_)
     release_host(q);
     srv->busy[q.slot] = 0;
     srv->used -= q.bytes;
+    if (q.ser) {
+        q.ser->refs -= 1;
+        q.ser->last_use = now_s();
+    }
     q.state = st_;
     q.t_done = now_s();
 }
@@ -218,13 +372,29 @@ bool advance(bps_server* srv, SReq& q)
     switch (q.state) {
         case S_STAGING: {
             if (cudaEventQuery(q.ev) != cudaSuccess) return false;
+            if (q.ser) {
+                SSeries& ser = *q.ser;
+                if (ser.staging) {  // the series' staging has completed (the event waited on it)
+                    if (ser.d_stage) {
+                        cudaFreeAsync(ser.d_stage, st);
+                        ser.d_stage = nullptr;
+                    }
+                    srv->used -= ser.stage_bytes;
+                    ser.staging = false;
+                    ser.resident = true;
+                    ser.s.mean = *ser.h_sum / (double)ser.n;
+                }
+                q.s = ser.s;
+            }
             if (q.d_stage) {
                 cudaFreeAsync(q.d_stage, st);
                 q.d_stage = nullptr;
             }
-            cudaFreeHost(q.h_series);
-            q.h_series = nullptr;
-            q.s.mean = *q.h_sum / (double)q.n;
+            if (q.h_series) {
+                cudaFreeHost(q.h_series);
+                q.h_series = nullptr;
+            }
+            if (!q.ser) q.s.mean = *q.h_sum / (double)q.n;
             q.job.reset(new Job());
             int rc = q.job->setup(srv->ctx, &q.s, &q.b, q.prm, st, q.d_cands, q.d_count,
                                   q.prm.cand_cap);
@@ -325,7 +495,12 @@ void worker_main(bps_server* srv)
                         slot = (int)i;
                         break;
                     }
-                if (slot < 0 || srv->used + q.bytes > srv->budget) break;
+                if (slot < 0) break;
+                size_t need = q.bytes;
+                if (q.ser && !q.ser->resident && !q.ser->staging)
+                    need += q.ser->bytes + q.ser->stage_bytes;
+                if (srv->used + need > srv->budget) make_room(srv, need, q.ser);
+                if (srv->used + need > srv->budget) break;
                 srv->queue.pop_front();
                 if (!admit_one(srv, q, slot)) {
                     cudaStreamSynchronize(srv->slots[slot]);
@@ -418,23 +593,41 @@ try {
         cudaStreamSynchronize(s);
         cudaStreamDestroy(s);
     }
+    {
+        std::lock_guard<std::recursive_mutex> cl(srv->ctx->mu);
+        for (auto& kv : srv->series) {
+            if (kv.second->resident || kv.second->staging) evict_series(srv, *kv.second);
+            free_series_host(*kv.second);
+        }
+        cudaStreamSynchronize(srv->ctx->stream);
+    }
     delete srv;
 } catch (...) {
 }
 
 const char* bps_server_last_error(bps_server* srv) { return srv ? srv->err.c_str() : "null server"; }
 
-int bps_server_submit(bps_server* srv, const float* series, int64_t n, double tsamp_s, int dtype,
-                      const bps_template* bank, int64_t count, const bps_search_params* params,
-                      int64_t* ticket)
-try {
-    if (!srv) return BPS_ERR_INVALID_ARG;
-    if (!series || !bank || !params || !ticket)
-        return sfail(srv, BPS_ERR_INVALID_ARG, "null pointer");
-    if (!is_pow2(n) || n < (1 << 11) || n > (1 << 25))
-        return sfail(srv, BPS_ERR_INVALID_ARG, "n must be a power of two in [2^11, 2^25]");
-    if (!(tsamp_s > 0.0) || !std::isfinite(tsamp_s) || (dtype != BPS_F32 && dtype != BPS_F16_SCALED))
-        return sfail(srv, BPS_ERR_INVALID_ARG, "bad tsamp or dtype");
+}  // extern "C"
+
+namespace {
+
+bool series_args_ok(int64_t n, double tsamp_s, int dtype)
+{
+    return is_pow2(n) && n >= (1 << 11) && n <= (1 << 25) && tsamp_s > 0.0 && std::isfinite(tsamp_s) &&
+           (dtype == BPS_F32 || dtype == BPS_F16_SCALED);
+}
+
+// Checks a request and builds its record (pinned host buffers, events, device bytes).
+// `own_series`: the request carries its own series copy (bps_server_submit), else it names
+// a resident series (bps_server_submit_series).
+int make_request(bps_server* srv, int64_t n, double tsamp_s, int dtype, const bps_template* bank,
+                 int64_t count, const bps_search_params* params, bool own_series,
+                 std::unique_ptr<SReq>& out)
+{
+    if (!bank || !params) return sfail(srv, BPS_ERR_INVALID_ARG, "null pointer");
+    if (!series_args_ok(n, tsamp_s, dtype))
+        return sfail(srv, BPS_ERR_INVALID_ARG, "n must be a power of two in [2^11, 2^25], tsamp > 0, "
+                                               "dtype BPS_F32 or BPS_F16_SCALED");
     if (count < 1 || count > (1ll << 31)) return sfail(srv, BPS_ERR_INVALID_ARG, "bad bank size");
     for (int64_t i = 0; i < count; ++i) {
         const bps_template& q = bank[i];
@@ -460,13 +653,15 @@ try {
         Plan p;
         int rc = make_plan(nullptr, hs, hb, *params, p);
         if (rc) return sfail(srv, rc, "orbits outside the FP32 index-map envelope or bad size");
-        q->bytes = request_bytes(p, count, *params, dtype);
+        q->bytes = request_bytes(p, count, *params, dtype, own_series);
     }
-    if (q->bytes > srv->budget)
+    size_t stg = 0;
+    const size_t total = q->bytes + (own_series ? 0 : series_bytes(n, dtype, &stg) + stg);
+    if (total > srv->budget)
         return sfail(srv, BPS_ERR_OUT_OF_MEMORY, "request needs %zu bytes, server budget %zu",
-                     q->bytes, srv->budget);
+                     total, srv->budget);
     cudaSetDevice(srv->ctx->device);
-    if (cudaMallocHost((void**)&q->h_series, 4 * (size_t)n) != cudaSuccess ||
+    if ((own_series && cudaMallocHost((void**)&q->h_series, 4 * (size_t)n) != cudaSuccess) ||
         cudaMallocHost((void**)&q->h_sum, sizeof(double)) != cudaSuccess ||
         cudaMallocHost((void**)&q->h_count, 2 * sizeof(unsigned long long)) != cudaSuccess ||
         cudaMallocHost((void**)&q->h_cands, sizeof(Cand) * (size_t)std::min<int64_t>(params->cand_cap, kPinnedCands)) != cudaSuccess ||
@@ -476,7 +671,12 @@ try {
     }
     q->grp.resize(srv->cfg.groups_in_flight);
     for (auto& e : q->grp) cudaEventCreateWithFlags(&e, cudaEventDisableTiming);
-    std::memcpy(q->h_series, series, 4 * (size_t)n);
+    out = std::move(q);
+    return BPS_OK;
+}
+
+void enqueue(bps_server* srv, std::unique_ptr<SReq>& q, int64_t* ticket)
+{
     q->t_submit = now_s();
     {
         std::lock_guard<std::mutex> lk(srv->mu);
@@ -486,6 +686,123 @@ try {
         srv->reqs[q->ticket] = std::move(q);
     }
     srv->cv.notify_all();
+}
+
+}  // namespace
+
+extern "C" {
+
+int bps_server_submit(bps_server* srv, const float* series, int64_t n, double tsamp_s, int dtype,
+                      const bps_template* bank, int64_t count, const bps_search_params* params,
+                      int64_t* ticket)
+try {
+    if (!srv) return BPS_ERR_INVALID_ARG;
+    if (!series || !ticket) return sfail(srv, BPS_ERR_INVALID_ARG, "null pointer");
+    std::unique_ptr<SReq> q;
+    int rc = make_request(srv, n, tsamp_s, dtype, bank, count, params, true, q);
+    if (rc) return rc;
+    std::memcpy(q->h_series, series, 4 * (size_t)n);
+    enqueue(srv, q, ticket);
+    return BPS_OK;
+} catch (...) {
+    return BPS_ERR_OUT_OF_MEMORY;  // host allocation failed
+}
+
+int bps_server_load_series(bps_server* srv, const float* series, int64_t n, double tsamp_s,
+                           int dtype, int64_t* series_id)
+try {
+    if (!srv) return BPS_ERR_INVALID_ARG;
+    if (!series || !series_id) return sfail(srv, BPS_ERR_INVALID_ARG, "null pointer");
+    if (!series_args_ok(n, tsamp_s, dtype))
+        return sfail(srv, BPS_ERR_INVALID_ARG, "n must be a power of two in [2^11, 2^25], tsamp > 0, "
+                                               "dtype BPS_F32 or BPS_F16_SCALED");
+    std::unique_ptr<SSeries> ser(new SSeries());
+    ser->n = n;
+    ser->tsamp = tsamp_s;
+    ser->dtype = dtype;
+    ser->bytes = series_bytes(n, dtype, &ser->stage_bytes);
+    if (ser->bytes + ser->stage_bytes > srv->budget)
+        return sfail(srv, BPS_ERR_OUT_OF_MEMORY, "series needs %zu bytes, server budget %zu",
+                     ser->bytes + ser->stage_bytes, srv->budget);
+    cudaSetDevice(srv->ctx->device);
+    if (cudaMallocHost((void**)&ser->h_series, 4 * (size_t)n) != cudaSuccess ||
+        cudaMallocHost((void**)&ser->h_sum, sizeof(double)) != cudaSuccess ||
+        cudaEventCreateWithFlags(&ser->ready, cudaEventDisableTiming) != cudaSuccess) {
+        free_series_host(*ser);
+        return sfail(srv, BPS_ERR_OUT_OF_MEMORY, "pinned host copy failed");
+    }
+    std::memcpy(ser->h_series, series, 4 * (size_t)n);
+    std::lock_guard<std::mutex> lk(srv->mu);
+    ser->id = srv->next_series++;
+    *series_id = ser->id;
+    srv->series[ser->id] = std::move(ser);
+    return BPS_OK;
+} catch (...) {
+    return BPS_ERR_OUT_OF_MEMORY;  // host allocation failed
+}
+
+int bps_server_submit_series(bps_server* srv, int64_t series_id, const bps_template* bank,
+                             int64_t count, const bps_search_params* params, int64_t* ticket)
+try {
+    if (!srv) return BPS_ERR_INVALID_ARG;
+    if (!ticket) return sfail(srv, BPS_ERR_INVALID_ARG, "null pointer");
+    SSeries* ser = nullptr;
+    {
+        std::lock_guard<std::mutex> lk(srv->mu);
+        auto it = srv->series.find(series_id);
+        if (it == srv->series.end())
+            return sfail(srv, BPS_ERR_INVALID_ARG, "unknown server series %lld", (long long)series_id);
+        ser = it->second.get();
+        ser->refs += 1;  // pinned from now on: not evicted or unloaded while named
+    }
+    std::unique_ptr<SReq> q;
+    int rc = make_request(srv, ser->n, ser->tsamp, ser->dtype, bank, count, params, false, q);
+    if (rc) {
+        std::lock_guard<std::mutex> lk(srv->mu);
+        ser->refs -= 1;
+        return rc;
+    }
+    q->ser = ser;
+    enqueue(srv, q, ticket);
+    return BPS_OK;
+} catch (...) {
+    return BPS_ERR_OUT_OF_MEMORY;  // host allocation failed
+}
+
+int bps_server_unload_series(bps_server* srv, int64_t series_id)
+try {
+    if (!srv) return BPS_ERR_INVALID_ARG;
+    std::lock_guard<std::mutex> lk(srv->mu);
+    auto it = srv->series.find(series_id);
+    if (it == srv->series.end())
+        return sfail(srv, BPS_ERR_INVALID_ARG, "unknown server series %lld", (long long)series_id);
+    SSeries& ser = *it->second;
+    if (ser.refs > 0)
+        return sfail(srv, BPS_ERR_INVALID_ARG, "server series %lld is named by %d unfinished requests",
+                     (long long)series_id, ser.refs);
+    {
+        std::lock_guard<std::recursive_mutex> cl(srv->ctx->mu);
+        cudaSetDevice(srv->ctx->device);
+        if (ser.resident || ser.staging) evict_series(srv, ser);
+        cudaStreamSynchronize(srv->ctx->stream);
+    }
+    free_series_host(ser);
+    srv->series.erase(it);
+    return BPS_OK;
+} catch (...) {
+    return BPS_ERR_OUT_OF_MEMORY;  // host allocation failed
+}
+
+int bps_server_series_info(bps_server* srv, int64_t series_id, int32_t* resident,
+                           int64_t* times_staged)
+try {
+    if (!srv) return BPS_ERR_INVALID_ARG;
+    std::lock_guard<std::mutex> lk(srv->mu);
+    auto it = srv->series.find(series_id);
+    if (it == srv->series.end())
+        return sfail(srv, BPS_ERR_INVALID_ARG, "unknown server series %lld", (long long)series_id);
+    if (resident) *resident = (it->second->resident || it->second->staging) ? 1 : 0;
+    if (times_staged) *times_staged = it->second->times_staged;
     return BPS_OK;
 } catch (...) {
     return BPS_ERR_OUT_OF_MEMORY;  // host allocation failed

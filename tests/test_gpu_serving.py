@@ -123,3 +123,60 @@ def test_nonblocking_result_and_invalid(bps, ctx):
             srv.submit(x[:3000], ts, bank, bps.default_params(), dt)
         with pytest.raises(bps.BpsError):
             srv.result(987654)
+
+
+def test_resident_series_same_results(bps, ctx):
+    """Requests on series held in the server's resident store return exactly the
+    candidates of requests that carry their own copy of the series; the series is staged
+    once and stays on the device."""
+    reqs = [r[:4] for r in _requests(bps)]
+    prm = bps.default_params(sigma_thr=5.0)
+    with bps.Server(ctx, max_active=4, groups_in_flight=2) as srv:
+        ref = [srv.result(srv.submit(x, ts, bank, prm, dt))[0] for x, ts, bank, dt in reqs]
+        ids = [srv.load_series(x, ts, dt) for x, ts, bank, dt in reqs]
+        assert not srv.series_info(ids[0])["resident"]
+        tickets = [srv.submit_series(i, bank, prm) for i, (_, _, bank, _) in zip(ids, reqs)]
+        tickets += [srv.submit_series(i, bank, prm) for i, (_, _, bank, _) in zip(ids, reqs)][::-1]
+        with pytest.raises(bps.BpsError):
+            srv.unload_series(ids[0])  # named by unfinished requests
+        res = [srv.result(t)[0] for t in tickets]
+        for i in range(len(reqs)):
+            assert np.array_equal(res[i], ref[i]), i
+            assert np.array_equal(res[2 * len(reqs) - 1 - i], ref[i]), i
+        for i in ids:
+            info = srv.series_info(i)
+            assert info["resident"] and info["times_staged"] == 1
+        srv.unload_series(ids[0])
+        with pytest.raises(bps.BpsError):
+            srv.submit_series(ids[0], reqs[0][2], prm)
+        with pytest.raises(bps.BpsError):
+            srv.series_info(987654)
+
+
+def test_resident_series_lru_eviction(bps, ctx):
+    """With an HBM budget that holds one 2^24-sample series beside a request but not two,
+    alternating requests evict the least recently used idle series and stage it again
+    from the server's host copy; results are unchanged."""
+    n, ts, K = 1 << 24, 64e-6, 4
+    T = n * ts
+    xs = [synth.noise(n, 600 + i) for i in range(2)]
+    bank, _ = synth.uniform_bank(K, 601, (3 * T, 10 * T), (0.0, 1.0))
+    prm = bps.default_params(sigma_thr=5.0, batch=K, cand_cap=1 << 10, log_cols=11,
+                             log_tile=14, log_tile2=13)
+    M = n // 2
+    # device bytes of one request (bank, workspace of K templates, candidates): the packed
+    # FFT intermediate, the power in bin order and row-major (C = 2048, 2^13 pass-2 tiles),
+    # anchors and block scales (< 1 MiB)
+    req = (M + 1) * 8 * K + 2 * M * 4 * K + (1 << 20)
+    ser = 4 * n
+    with bps.Server(ctx, max_active=1, groups_in_flight=2, hbm_budget=req + ser + ser // 2) as srv:
+        ids = [srv.load_series(x, ts) for x in xs]
+        order = [0, 1, 0, 0, 1]
+        out = [srv.result(srv.submit_series(ids[j], bank, prm))[0] for j in order]
+        staged = [srv.series_info(i)["times_staged"] for i in ids]
+        assert staged == [2, 2], staged
+        assert srv.stats()["bytes_held"] == ser  # the last series used stays resident
+    with bps.Server(ctx, max_active=1) as big:
+        ref = [big.result(big.submit(x, ts, bank, prm))[0] for x in xs]
+    for j, c in zip(order, out):
+        assert np.array_equal(c, ref[j]), j
