@@ -60,6 +60,8 @@ def parse():
                     help="series storage on the device: f32, or f16 with a power-of-two "
                          "scale per 4096 samples (FFT arithmetic is FP32 either way)")
     ap.add_argument("--no-plain", action="store_true")
+    ap.add_argument("--no-f16", action="store_true",
+                    help="skip the FP16-storage line of the same request")
     ap.add_argument("--no-serving", action="store_true")
     ap.add_argument("--serve-rates", default="1,2,5,10,20,50",
                     help="Poisson request rates (req/s) of the serving sweep")
@@ -219,6 +221,27 @@ def oracle_rate(x, tsamp, bank, threads):
     return bank.shape[0] / dt, dt
 
 
+def f16_oracle_error(ctx, sid16, bid, w, bank, count=2):
+    """Whitened-power and harmonic-sum error of the FP16-storage path against the FP64
+    oracle on the FP32 series, for the first `count` injected orbits of the bank (the
+    oracle on the GPU's index map), in the units of the parity tests: |dPw| / max(1, Pw)
+    and |dS| / (n + S) per harmonic level."""
+    import oracle
+    n = w.n
+    pw_err, s_err = 0.0, [0.0] * 5
+    tis = [int(t) for t in w.true_idx if t < bank.shape[0]][:count]
+    for ti in tis:
+        gi = ctx.index_map(sid16, bid, ti, n)[0].astype(np.int64)
+        r = oracle.search_template(w.series, w.tsamp, bank[ti], want_arrays=True, idx_in=gi)
+        pw = ctx.whitened_spectrum(sid16, bid, ti, 1, n)[0].astype(np.float64)
+        S = ctx.harmonic_sums(sid16, bid, ti, n).astype(np.float64)
+        pw_err = max(pw_err, float(np.max(np.abs(pw - r["Pw"]) / np.maximum(1.0, r["Pw"]))))
+        for L in range(5):
+            s_err[L] = max(s_err[L], float(np.max(np.abs(S[L] - r["S"][L]) / ((1 << L) + r["S"][L]))))
+    return {"templates": tis, "pw_rel_max": pw_err,
+            "harmonic_sum_rel_max_per_level": dict(zip(["1", "2", "4", "8", "16"], s_err))}
+
+
 def cpu_threads(args):
     c = os.cpu_count() or 1
     return args.cpu_threads or max(1, min(c, 32))
@@ -262,7 +285,8 @@ def serving_pool(seed=5):
 
 def run_serving(bps, ctx, rate, nreq, pool, seed=5):
     """Poisson stream of search requests into the continuously batched server: series
-    2^20..2^24 samples (log-uniform) at 64 us stored FP16, banks of 64..4096 (log-uniform)
+    2^20..2^24 samples (log-uniform) at 64 us stored FP16 and held in the server's
+    resident store (loaded once, before the stream), banks of 64..4096 (log-uniform)
     circular or elliptical (e <= 0.1) templates.  Returns throughput and p50/p99 latency
     (submission to candidates on the host)."""
     import threading
@@ -275,11 +299,18 @@ def run_serving(bps, ctx, rate, nreq, pool, seed=5):
         K = int(2 ** rng.uniform(6, 12))
         ecc = (0.0, 0.1) if rng.random() < 0.5 else None
         bank, _ = synth.uniform_bank(K, 1000 + i, (3 * T, 10 * T), (0.0, 0.5), ecc=ecc)
-        reqs.append((pool[logn][i % 3], ts, bank))
+        reqs.append(((logn, i % 3), bank))
     gaps = rng.exponential(1.0 / rate, nreq)
     prm = bps.default_params(cand_cap=1 << 16)
     lat, tickets = [], []
     with bps.Server(ctx, max_active=4, groups_in_flight=2) as srv:
+        sids = {(logn, j): srv.load_series(x, 64e-6, bps.BPS_F16_SCALED)
+                for logn, xs in pool.items() for j, x in enumerate(xs)}
+        # stage every series once (one small request each) so the stream finds them resident
+        warm = [srv.submit_series(sid, np.array([(1e4, 0.0, 0.0, 0.0, 0.0)]), prm)
+                for sid in sids.values()]
+        for t in warm:
+            srv.result(t, allow_overflow=True)
         t_start = time.perf_counter()
         done = threading.Event()
 
@@ -294,16 +325,16 @@ def run_serving(bps, ctx, rate, nreq, pool, seed=5):
         th = threading.Thread(target=collect)
         th.start()
         t_next = t_start
-        for (x, ts, bank), g in zip(reqs, gaps):
+        for (key, bank), g in zip(reqs, gaps):
             t_next += g
             d = t_next - time.perf_counter()
             if d > 0:
                 time.sleep(d)
-            tickets.append(srv.submit(x, ts, bank, prm, bps.BPS_F16_SCALED))
+            tickets.append(srv.submit_series(sids[key], bank, prm))
         done.wait()
         th.join()
         wall = time.perf_counter() - t_start
-    templates = sum(r[2].shape[0] for r in reqs)
+    templates = sum(r[1].shape[0] for r in reqs)
     return {"rate_req_s": rate, "requests": nreq, "templates": templates,
             "templates_per_s": templates / wall, "wall_s": wall,
             "p50_ms": 1e3 * float(np.percentile(lat, 50)),
@@ -311,6 +342,7 @@ def run_serving(bps, ctx, rate, nreq, pool, seed=5):
 
 
 SERVING_WORKLOAD = ("Poisson arrivals; series 2^20-2^24 (log-uniform) x 64 us, FP16 storage, "
+                    "resident in the server (15 series loaded and staged before the stream), "
                     "one in three with an injected pulsar-BH binary; "
                     "banks 64-4096 (log-uniform) circular or elliptical (e <= 0.1) templates; "
                     "server max_active 4, 2 launch groups in flight per request, HBM budget "
@@ -516,6 +548,26 @@ def main():
                                        for k in bps.STAGES},
                  "form": "index map + gather kernel -> cuFFT R2C -> power -> same median/harmonic-sum kernels, one template per launch"}
 
+    # the mixed-precision form at the same request: the series stored FP16 with a
+    # power-of-two scale per 4096 samples, FP32 FFT arithmetic (same kernels and shape)
+    f16 = None
+    if args.dtype == "f32" and not args.no_f16:
+        sid16 = ctx.load_series(w.series, w.tsamp, bps.BPS_F16_SCALED)
+        sid_main = sid
+        sid = sid16
+        hms, hstats, hc = timed_steps(0, args.steps, 2, True)
+        sid = sid_main
+        htot = allmax(ws, sum(hms) / 1e3)
+        f16 = {"value": K * ws * len(hms) / htot, "unit": UNIT, "ms_per_step": statistics.mean(hms),
+               "candidates": hc, "storage": "FP16 + power-of-two FP32 scale per 4096 samples",
+               "arithmetic": "f32",
+               "stage_ms_per_step": {k: sum(s_["stage_ms"][k] for s_ in hstats) / len(hstats)
+                                     for k in bps.STAGES},
+               "speedup_vs_plain": None, "speedup_vs_f32_storage": None}
+        f16["speedup_vs_f32_storage"] = f16["value"] / value
+        if plain:
+            f16["speedup_vs_plain"] = f16["value"] / plain["value"]
+
     # end to end through the public API with host buffers: pinned series H2D, bank, search,
     # candidate D2H, unload -- every step.
     pinned = torch.from_numpy(w.series).pin_memory()
@@ -575,6 +627,8 @@ def main():
         cpu = {"value": rate, "unit": UNIT, "cores": thr, "kind": "oracle",
                "sample": "%d of %d templates of the 2^%d-sample workload (%.1f s)" % (
                    nt, K, args.logn, dt)}
+        if f16 is not None:
+            f16["error_vs_oracle"] = f16_oracle_error(ctx, sid16, bid, w, bank)
 
     serving = None
     if not args.no_serving and ws == 1:
@@ -595,6 +649,7 @@ def main():
            "latency_ms": {"p50": float(np.percentile(ms, 50)), "p99": float(np.percentile(ms, 99))},
            "plain_form": plain,
            "speedup_vs_plain": (value / plain["value"]) if plain else None,
+           "f16_headline": f16,
            "roofline": roof,
            "path_roofline": {"achieved": path_gbs, "peak": peak, "unit": "GB/s",
                              "frac": path_gbs / peak, "alg_bytes_per_template": PATH_BYTES_PER_N * n},

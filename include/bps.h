@@ -97,7 +97,27 @@ typedef struct {
                            /* length R, pass-2 row length C: the radix structure of   */
                            /* both passes), in [max(5, log2(N/2) - 12),               */
                            /* min(log2(N/2) - 5, 12)]; 0 = library's choice           */
+    int32_t pass1_kind;    /* BPS_PASS1_*: how pass 1 (index map + gather + column FFTs) */
+                           /* is organised; 0 = library's choice                        */
+    int32_t power_layout;  /* BPS_POWER_*: how pass 2 stores the power spectrum;        */
+                           /* 0 = library's choice                                      */
 } bps_search_params;
+
+/* bps_search_params.pass1_kind */
+#define BPS_PASS1_AUTO      0  /* the autotuned choice, else the one-phase kernel            */
+#define BPS_PASS1_FUSED     1  /* one phase per tile: every warp gathers, then all run the   */
+                               /* FFT stages (tiles of 2^log_tile complex values)            */
+#define BPS_PASS1_WARPSPEC  2  /* warp-specialised: producer warps gather tile i+1 while     */
+                               /* consumer warps FFT tile i (2^13-complex tiles; built for   */
+                               /* R = 2^10..2^12 and 2^21..2^25 samples, else INVALID_ARG)   */
+
+/* bps_search_params.power_layout (results are identical; only the memory traffic differs) */
+#define BPS_POWER_AUTO      0  /* row-major when a pass-2 CTA holds at most two row pairs,   */
+                               /* W <= R and W <= 1024, else bin order                       */
+#define BPS_POWER_BINS      1  /* pass 2 writes bins in order; whitening in place            */
+#define BPS_POWER_ROWS      2  /* pass 2 writes row-major blocks of 8 columns; the whitening */
+                               /* kernel transposes (needs <= 2 row pairs per pass-2 CTA,    */
+                               /* W <= R, W <= 1024, else INVALID_ARG)                       */
 
 typedef struct bps_ctx bps_ctx;
 

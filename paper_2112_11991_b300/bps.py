@@ -32,6 +32,12 @@ BPS_F32 = 0
 BPS_F16_SCALED = 1
 BPS_MODE_FUSED = 0
 BPS_MODE_PLAIN = 1
+BPS_PASS1_AUTO = 0
+BPS_PASS1_FUSED = 1
+BPS_PASS1_WARPSPEC = 2
+BPS_POWER_AUTO = 0
+BPS_POWER_BINS = 1
+BPS_POWER_ROWS = 2
 
 EXPORTED = ["bps_default_params", "bps_create", "bps_destroy", "bps_load_series",
             "bps_load_bank", "bps_search", "bps_query", "bps_fetch_candidates",
@@ -75,7 +81,8 @@ class bps_search_params(C.Structure):
     _fields_ = [("nharm_max", C.c_int32), ("whiten_block", C.c_int32), ("sigma_thr", C.c_double),
                 ("auto_thr", C.c_int32), ("mode", C.c_int32), ("cand_cap", C.c_int64),
                 ("precision", C.c_int32), ("batch", C.c_int32), ("log_tile", C.c_int32),
-                ("log_tile2", C.c_int32), ("log_cols", C.c_int32)]
+                ("log_tile2", C.c_int32), ("log_cols", C.c_int32), ("pass1_kind", C.c_int32),
+                ("power_layout", C.c_int32)]
 
 
 class bps_server_config(C.Structure):

@@ -649,17 +649,25 @@ try {
     if (base->log_cols) splits.push_back(base->log_cols);
     else if (base->mode == BPS_MODE_PLAIN) splits.push_back(0);
     else
-        for (int d : {0, -1, 1})
+        for (int d : {0, -1, 1, 2})
             if (log_cols_ok(logM, default_log_cols(logM) + d)) splits.push_back(default_log_cols(logM) + d);
     double best_ms = 1e30;
     bps_search_params bp = *base;
+    // pass 1: the one-phase kernel at both tiles, and the warp-specialised one where built
+    std::vector<std::pair<int, int>> p1;  // (kind, tile)
+    if (base->pass1_kind != BPS_PASS1_WARPSPEC)
+        for (int t : tiles) p1.push_back({BPS_PASS1_FUSED, t});
+    if (base->mode == BPS_MODE_FUSED && base->pass1_kind != BPS_PASS1_FUSED) p1.push_back({BPS_PASS1_WARPSPEC, 13});
     for (int lc : splits)
-    for (int t1 : tiles)
+    for (auto k1 : p1)
         for (int t2 : tiles)
             for (int nb : batches) {
                 if (nb > sub.K) continue;
+                const int lcx = lc ? lc : default_log_cols(logM);
+                if (k1.first == BPS_PASS1_WARPSPEC && !ws_pass1_built(logM - lcx, lcx)) continue;
                 bps_search_params pr = *base;
-                pr.log_tile = t1;
+                pr.pass1_kind = k1.first;
+                pr.log_tile = k1.second;
                 pr.log_tile2 = t2;
                 pr.log_cols = lc;
                 pr.batch = nb;
@@ -688,8 +696,8 @@ try {
     cudaFree(cd);
     cudaFree(cnt);
     if (rc) return rc;
-    ctx->tuned[tune_key(ilog2(s->n), base->mode, ilog2(base->nharm_max))] = {bp.log_tile, bp.log_tile2,
-                                                                          bp.batch, bp.log_cols};
+    ctx->tuned[tune_key(ilog2(s->n), base->mode, ilog2(base->nharm_max))] = {
+        bp.log_tile, bp.log_tile2, bp.batch, bp.log_cols, bp.pass1_kind, bp.power_layout};
     *best = bp;
     if (best_ms_per_template) *best_ms_per_template = best_ms / (double)sub.K;
     return BPS_OK;
@@ -757,14 +765,21 @@ try {
     const int nt = (int)count;
     if ((rc = ws_alloc(ctx, p, nt, params->mode, st, w))) return rc;
     float* out = nullptr;
+    unsigned long long* stw = nullptr;
+    unsigned long long stv = 0;
     CK(pool_alloc(ctx, (void**)&out, sizeof(float) * p.M * nt, st));
+    CK(pool_alloc(ctx, (void**)&stw, sizeof(unsigned long long), st));
+    CK(cudaMemsetAsync(stw, 0, sizeof(unsigned long long), st));
     StageTimer tm;
-    if ((rc = run_spectrum(ctx, *s, *b, p, params->mode, t0, nt, w, st, tm))) return rc;
+    if ((rc = run_spectrum(ctx, *s, *b, p, params->mode, t0, nt, w, st, tm, stw))) return rc;
     CK(launch_whitened(w.P, w.scale, nt, p, out, st));
     CK(cudaMemcpyAsync(pw_out, out, sizeof(float) * p.M * nt, cudaMemcpyDeviceToHost, st));
+    CK(cudaMemcpyAsync(&stv, stw, sizeof stv, cudaMemcpyDeviceToHost, st));
     CK(cudaFreeAsync(out, st));
+    CK(cudaFreeAsync(stw, st));
     CK(cudaFreeAsync(w.base, st));
     CK(cudaStreamSynchronize(st));
+    if (stv) return fail(ctx, BPS_ERR_TIMEOUT, "a bounded device wait expired; spectrum incomplete");
     return BPS_OK;
 } catch (...) {
     return BPS_ERR_OUT_OF_MEMORY;  // host allocation failed
@@ -796,16 +811,19 @@ try {
     CK(pool_alloc(ctx, (void**)&cnt, 2 * sizeof(unsigned long long), st));
     CK(cudaMemsetAsync(cnt, 0, 2 * sizeof(unsigned long long), st));
     StageTimer tm;
-    if ((rc = run_spectrum(ctx, *s, *b, p, params->mode, template_idx, 1, w, st, tm))) return rc;
+    if ((rc = run_spectrum(ctx, *s, *b, p, params->mode, template_idx, 1, w, st, tm, cnt + 1))) return rc;
     Thr th;
     for (int L = 0; L < 5; ++L) th.v[L] = INFINITY;
     CK(launch_harmsum(w.P, w.scale, 1, template_idx, p, th, cd, 1, cnt, so, st));
+    unsigned long long cs[2] = {0, 0};
     CK(cudaMemcpyAsync(s_out, so, sizeof(float) * p.M * p.nlev, cudaMemcpyDeviceToHost, st));
+    CK(cudaMemcpyAsync(cs, cnt, sizeof cs, cudaMemcpyDeviceToHost, st));
     CK(cudaFreeAsync(so, st));
     CK(cudaFreeAsync(cd, st));
     CK(cudaFreeAsync(cnt, st));
     CK(cudaFreeAsync(w.base, st));
     CK(cudaStreamSynchronize(st));
+    if (cs[1]) return fail(ctx, BPS_ERR_TIMEOUT, "a bounded device wait expired; sums incomplete");
     return BPS_OK;
 } catch (...) {
     return BPS_ERR_OUT_OF_MEMORY;  // host allocation failed

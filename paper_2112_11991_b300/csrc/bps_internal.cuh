@@ -59,8 +59,18 @@ struct Plan {
     int nlev;       // log2(nharm) + 1
     int ptrans;     // 1: pass 2 writes the power row-major by k1, P'[k1 C + k2] for bin
                     // k1 + R k2, and the median kernel transposes it into bin order
+    int p1ws;       // 1: warp-specialised pass 1 (producer warps gather, consumer warps FFT)
     double tsamp;
 };
+
+// Four-step splits (log R, log C) the warp-specialised pass 1 is built for (2^13-complex
+// tiles of 2^(13 - log R) columns).
+inline bool ws_pass1_built(int logR, int logC)
+{
+    const int lm = logR + logC;
+    return (logR == 10 || logR == 11 || logR == 12) && logC >= 13 - logR && lm >= 20 && lm <= 24 &&
+           logC <= 12;
+}
 
 // Four-step split of the packed FFT, M = R * C, with CTA tiles of 2^logTile (pass 1)
 // and 2^logTile2 (pass 2) complex values in shared memory (13: 256 threads, two CTAs
@@ -93,6 +103,7 @@ inline void plan_geometry(Plan& p, int logTile = 14, int logTile2 = 13, int logC
     p.logNP = (logTile2 - 1 - p.logC) < (p.logR - 1) ? (logTile2 - 1 - p.logC) : (p.logR - 1);
     if (p.logNP < 0) p.logNP = 0;
     p.ptrans = 0;
+    p.p1ws = 0;
 }
 
 // Anchor block length B = 2^logB: the largest (<= 2^14, <= n) for which every
@@ -154,8 +165,10 @@ cudaError_t prepare_detect_kernels();
 // One CTA polls an mbarrier that never completes at most `limit` times; status[0] = 1
 // when the wait expired (the bounded-wait path of the harmonic sum, exercised safely).
 cudaError_t launch_wait_selftest(int limit, unsigned long long* status, cudaStream_t s);
+// status: a device word of the request; the warp-specialised form sets bit 1 when one of
+// its bounded mbarrier waits expired (unused by the one-phase form)
 cudaError_t launch_pass1(const SeriesView& x, const Anchor* anc, int nt, const Plan& p,
-                         const float2* tw, float2* Y, cudaStream_t s);
+                         const float2* tw, float2* Y, unsigned long long* status, cudaStream_t s);
 cudaError_t launch_pass2(const float2* Y, int nt, const Plan& p, const float2* tw,
                          float* P, cudaStream_t s);
 cudaError_t launch_power_from_r2c(const float2* X, int nt, const Plan& p, float* P,

@@ -88,8 +88,9 @@ struct bps_ctx {
     std::map<bps::rt::FftKey, cufftHandle> ffts;
     float2* tw = nullptr;
     bool profiling = false;
-    // autotuned launch shapes per (log2 n, mode, log2 nharm): tile1, tile2, batch, log C
-    std::map<int, std::array<int, 4>> tuned;
+    // autotuned launch shapes per (log2 n, mode, log2 nharm): tile1, tile2, batch, log C,
+    // pass-1 kind, power layout
+    std::map<int, std::array<int, 6>> tuned;
     std::map<int64_t, bps::rt::GraphObj*> graphs;
 };
 
@@ -183,6 +184,10 @@ inline int check_params(bps_ctx* ctx, const bps_search_params* pr, int64_t n)
     if (pr->log_cols != 0 && !log_cols_ok(ilog2(n) - 1, pr->log_cols))
         return fail(ctx, BPS_ERR_INVALID_ARG, "log_cols %d is not a valid split of %lld samples",
                     pr->log_cols, (long long)n);
+    if (pr->pass1_kind < BPS_PASS1_AUTO || pr->pass1_kind > BPS_PASS1_WARPSPEC)
+        return fail(ctx, BPS_ERR_INVALID_ARG, "unknown pass1_kind %d", pr->pass1_kind);
+    if (pr->power_layout < BPS_POWER_AUTO || pr->power_layout > BPS_POWER_ROWS)
+        return fail(ctx, BPS_ERR_INVALID_ARG, "unknown power_layout %d", pr->power_layout);
     return BPS_OK;
 }
 
@@ -210,25 +215,52 @@ inline int make_plan(bps_ctx* ctx, const Series& s, const Bank& b, const bps_sea
     p.logn = ilog2(s.n);
     p.M = s.n / 2;
     p.logM = p.logn - 1;
-    int t1 = 14, t2 = 13, lc = 0;
+    int t1 = 14, t2 = 13, lc = 0, p1k = BPS_PASS1_FUSED, pl = BPS_POWER_AUTO;
+    bool tuned = false;
     if (ctx) {
         auto it = ctx->tuned.find(tune_key(ilog2(s.n), pr.mode, ilog2(pr.nharm_max)));
         if (it != ctx->tuned.end()) {
             t1 = it->second[0];
             t2 = it->second[1];
             lc = it->second[3];
+            p1k = it->second[4];
+            pl = it->second[5];
+            tuned = true;
         }
     }
     plan_geometry(p, pr.log_tile ? pr.log_tile : t1, pr.log_tile2 ? pr.log_tile2 : t2,
                   pr.log_cols ? pr.log_cols : lc);
     p.logW = ilog2(pr.whiten_block);
+    // pass-1 organisation: the caller's, else the autotuned one (when the caller left the
+    // split and tiles to the library too), else the one-phase kernel
+    int kind = pr.pass1_kind;
+    if (kind == BPS_PASS1_AUTO)
+        kind = (tuned && !pr.log_cols && !pr.log_tile) ? p1k : BPS_PASS1_FUSED;
+    if (pr.mode == BPS_MODE_FUSED && kind == BPS_PASS1_WARPSPEC) {
+        if (!ws_pass1_built(p.logR, p.logC)) {
+            if (pr.pass1_kind == BPS_PASS1_WARPSPEC)
+                return fail(ctx, BPS_ERR_INVALID_ARG,
+                            "the warp-specialised pass 1 is not built for R = 2^%d, C = 2^%d",
+                            p.logR, p.logC);
+        } else {
+            p.p1ws = 1;
+        }
+    }
     // row-major power (in groups of NP rows) when a pass-2 CTA holds at most two row pairs,
     // whose bin-order stores would be runs of one or two words, a whitening block lies
     // within one k2 (W <= R) and the warp median applies (W <= 1024).  Measured at 2^23,
     // C = 2048: NP = 2 pass 2 + median 14.5 + 7.7 us (bin order 21.1 + 5.4); NP = 4
     // 17.0 + 7.4 (bin order 18.5 + 5.4).
-    p.ptrans = (pr.mode == BPS_MODE_FUSED && p.logW <= 10 && p.logW <= p.logR && p.logNP <= 1)
-                   ? 1 : 0;
+    const bool rows_ok = pr.mode == BPS_MODE_FUSED && p.logW <= 10 && p.logW <= p.logR && p.logNP <= 1;
+    int layout = pr.power_layout;
+    if (layout == BPS_POWER_AUTO && tuned && !pr.log_cols && !pr.log_tile2) layout = pl;
+    if (layout == BPS_POWER_ROWS && !rows_ok) {
+        if (pr.power_layout == BPS_POWER_ROWS)
+            return fail(ctx, BPS_ERR_INVALID_ARG,
+                        "row-major power needs at most two row pairs per pass-2 CTA, W <= R and W <= 1024");
+        layout = BPS_POWER_AUTO;
+    }
+    p.ptrans = layout == BPS_POWER_BINS ? 0 : (layout == BPS_POWER_ROWS ? 1 : (rows_ok ? 1 : 0));
     p.nharm = pr.nharm_max;
     p.lognh = ilog2(pr.nharm_max);
     p.nlev = p.lognh + 1;
@@ -401,7 +433,7 @@ struct StageTimer {
 // or (plain) resample/cuFFT/power -> block medians.  P and scale are left in w.
 inline int run_spectrum(bps_ctx* ctx, const Series& s, const Bank& b, const Plan& p, int mode,
                  int64_t t0, int nt, Workspace& w, cudaStream_t st, StageTimer& tm,
-                 const Anchor* anc = nullptr)
+                 unsigned long long* status, const Anchor* anc = nullptr)
 {
     if (!anc) {
         tm.begin(BPS_STAGE_ANCHORS);
@@ -412,7 +444,7 @@ inline int run_spectrum(bps_ctx* ctx, const Series& s, const Bank& b, const Plan
     const SeriesView v = view_of(s);
     if (mode == BPS_MODE_FUSED) {
         tm.begin(BPS_STAGE_PASS1);
-        CK(launch_pass1(v, anc, nt, p, ctx->tw, w.Y, st));
+        CK(launch_pass1(v, anc, nt, p, ctx->tw, w.Y, status, st));
         tm.end();
         tm.begin(BPS_STAGE_PASS2);
         CK(launch_pass2(w.Y, nt, p, ctx->tw, p.ptrans ? w.Pt : w.P, st));
@@ -517,7 +549,7 @@ struct Job {
                 return fail(ctx, BPS_ERR_CUDA, "anchor launch: %s", cudaGetErrorString(e));
         }
         const int cnt = (int)std::min<int64_t>(nt, c0 + ccnt - t0);
-        int rc = run_spectrum(ctx, *s, *b, p, mode, t0, cnt, w, st, tm,
+        int rc = run_spectrum(ctx, *s, *b, p, mode, t0, cnt, w, st, tm, count + 1,
                               w.anc + (t0 - c0) * p.nanchor);
         if (rc) return rc;
         tm.begin(BPS_STAGE_HARMSUM);

@@ -17,6 +17,7 @@
 #include <mutex>
 
 #include "bps_internal.cuh"
+#include "mbar.cuh"
 
 namespace bps {
 
@@ -270,58 +271,6 @@ __global__ void __launch_bounds__(32 * kMedCols) k_median_warp_t(const float* __
 template <int VPL>
 constexpr size_t med_t_smem() { return sizeof(uint32_t) * ((size_t)32 * VPL * (kMedCols + 1) + 288 * kMedCols); }
 
-// ---- TMA bulk copies into shared memory, completed on an mbarrier (inline PTX) ----
-__device__ __forceinline__ uint32_t smem_u32(const void* p)
-{
-    return (uint32_t)__cvta_generic_to_shared(p);
-}
-
-__device__ __forceinline__ void mbar_init(uint64_t* bar, uint32_t count)
-{
-    asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_u32(bar)), "r"(count)
-                 : "memory");
-    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
-}
-
-__device__ __forceinline__ void mbar_expect_tx(uint64_t* bar, uint32_t bytes)
-{
-    asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(smem_u32(bar)),
-                 "r"(bytes)
-                 : "memory");
-}
-
-// 1D bulk copy global -> shared (16-byte aligned addresses, size a multiple of 16)
-__device__ __forceinline__ void tma_load_1d(void* dst, const void* src, uint32_t bytes,
-                                            uint64_t* bar)
-{
-    asm volatile(
-        "cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::"r"(
-            smem_u32(dst)),
-        "l"(src), "r"(bytes), "r"(smem_u32(bar))
-        : "memory");
-}
-
-__device__ __forceinline__ bool mbar_try_wait(uint64_t* bar, uint32_t phase)
-{
-    uint32_t ok;
-    asm volatile(
-        "{\n .reg .pred p;\n mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n"
-        " selp.u32 %0, 1, 0, p;\n}\n"
-        : "=r"(ok)
-        : "r"(smem_u32(bar)), "r"(phase)
-        : "memory");
-    return ok != 0;
-}
-
-constexpr int kWaitLimit = 1 << 22;
-
-// Bounded wait for the given phase parity of an mbarrier; false after `limit` polls.
-__device__ __forceinline__ bool mbar_wait_parity(uint64_t* bar, uint32_t parity, int limit = kWaitLimit)
-{
-    for (int it = 0; it < limit; ++it)
-        if (mbar_try_wait(bar, parity)) return true;
-    return false;
-}
 
 // Self-test of the bounded waits: an mbarrier expecting one arrival that nothing makes,
 // so its phase never completes; thread 0 polls it at most `limit` times with the same
@@ -336,11 +285,6 @@ __global__ void k_wait_selftest(int limit, unsigned long long* status)
     }
 }
 
-// Arrive on an mbarrier (release; one arrival).
-__device__ __forceinline__ void mbar_arrive(uint64_t* bar)
-{
-    asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(smem_u32(bar)) : "memory");
-}
 
 // Incoherent harmonic sum of the whitened spectrum over tiles of kHsTile = 1024 bins.
 // With H = nharm_max the h-th term of bin k is Pw[(k h + H/2) div H].  For a tile

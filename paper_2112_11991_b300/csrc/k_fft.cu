@@ -16,11 +16,14 @@
 // and run radix-16 Stockham stages with register butterflies, closed by one
 // radix-8/4/2 stage; each thread keeps its EPT = 32 elements in registers across
 // the barrier between the read and the write of a stage.
+#include <algorithm>
+#include <climits>
 #include <cmath>
 #include <mutex>
 
 #include "bps_internal.cuh"
 #include "index_map.cuh"
+#include "mbar.cuh"
 
 namespace bps {
 
@@ -120,13 +123,24 @@ struct Radix<4> {
     static constexpr __device__ __forceinline__ int out_pos(int s) { return 4 * (s & 3) + (s >> 2); }
 };
 
+// Barrier policies of the shared-memory FFT stages: the whole CTA, or the named barrier
+// ID of the N threads that run the FFT (the consumer warps of a warp-specialised CTA).
+struct SyncCTA {
+    static __device__ __forceinline__ void sync() { __syncthreads(); }
+};
+template <int ID, int N>
+struct SyncNamed {
+    static __device__ __forceinline__ void sync() { asm volatile("bar.sync %0, %1;" ::"n"(ID), "n"(N) : "memory"); }
+};
+
 // One Stockham stage of radix 2^LOGRADIX over 2^lognl lines of length L = 2^logL in
 // shared memory; element (line, pos) lives at buf[pad(line*ls + pos*es) + line*skew].
 // Ns = 2^logNs is the length of the sub-transforms already done.
-// blockDim.x * EPT == lines * L.
-template <int LOGRADIX, int EPT, bool LINE_FAST>
+// (threads running the stage) * EPT == lines * L; tid is the thread's index among them.
+template <int LOGRADIX, int EPT, bool LINE_FAST, class SYNC = SyncCTA>
 __device__ __forceinline__ void fft_stage(float2* buf, int logL, int logNs, int lognl,
-                                          int ls, int es, int skew, const float2* __restrict__ tw)
+                                          int ls, int es, int skew, const float2* __restrict__ tw,
+                                          int tid)
 {
     constexpr int RADIX = 1 << LOGRADIX;
     constexpr int BPT = EPT / RADIX;
@@ -143,7 +157,7 @@ __device__ __forceinline__ void fft_stage(float2* buf, int logL, int logNs, int 
     int dst[BPT], lskv[BPT];
 #pragma unroll
     for (int i = 0; i < BPT; ++i) {
-        const int b = threadIdx.x + i * nthr;
+        const int b = tid + i * nthr;
         int line, j;
         if (LINE_FAST) {
             line = b & ((1 << lognl) - 1);
@@ -175,7 +189,7 @@ __device__ __forceinline__ void fft_stage(float2* buf, int logL, int logNs, int 
         dst[i] = line * ls + (((j >> logNs) << (logNs + LOGRADIX)) + k) * es;
         lskv[i] = lsk;
     }
-    __syncthreads();
+    SYNC::sync();
     const int nse = Ns * es;
 #pragma unroll
     for (int i = 0; i < BPT; ++i) {
@@ -184,7 +198,7 @@ __device__ __forceinline__ void fft_stage(float2* buf, int logL, int logNs, int 
         for (int s = 0; s < RADIX; ++s)
             buf[pad(dst[i] + s * nse) + lskv[i]] = v[i * RADIX + Radix<LOGRADIX>::out_pos(s)];
     }
-    __syncthreads();
+    SYNC::sync();
 }
 
 // Radix-16 stages, then one radix-8/4/2 stage for the remaining factor.
@@ -194,11 +208,11 @@ __device__ __forceinline__ void smem_fft(float2* buf, int logL, int lognl, int l
 {
     int logNs = 0;
     for (; logNs + 4 <= logL; logNs += 4)
-        fft_stage<4, EPT, LINE_FAST>(buf, logL, logNs, lognl, ls, es, skew, tw);
+        fft_stage<4, EPT, LINE_FAST>(buf, logL, logNs, lognl, ls, es, skew, tw, threadIdx.x);
     const int rem = logL - logNs;
-    if (rem == 3) fft_stage<3, EPT, LINE_FAST>(buf, logL, logNs, lognl, ls, es, skew, tw);
-    else if (rem == 2) fft_stage<2, EPT, LINE_FAST>(buf, logL, logNs, lognl, ls, es, skew, tw);
-    else if (rem == 1) fft_stage<1, EPT, LINE_FAST>(buf, logL, logNs, lognl, ls, es, skew, tw);
+    if (rem == 3) fft_stage<3, EPT, LINE_FAST>(buf, logL, logNs, lognl, ls, es, skew, tw, threadIdx.x);
+    else if (rem == 2) fft_stage<2, EPT, LINE_FAST>(buf, logL, logNs, lognl, ls, es, skew, tw, threadIdx.x);
+    else if (rem == 1) fft_stage<1, EPT, LINE_FAST>(buf, logL, logNs, lognl, ls, es, skew, tw, threadIdx.x);
 }
 
 __global__ void k_twiddle_init(float2* tw)
@@ -381,13 +395,255 @@ __global__ void __launch_bounds__(512, 1) k_pass1(SeriesView x, const Anchor* __
     __syncthreads();
     int logNs = 4;
     for (; logNs + 4 < logR; logNs += 4)
-        fft_stage<4, kEPT, true>(sm, logR, logNs, logG, 1, G, 0, tw);
+        fft_stage<4, kEPT, true>(sm, logR, logNs, logG, 1, G, 0, tw, threadIdx.x);
     float2* Yt = Y + ((int64_t)tl << logM);
     switch (logR - logNs) {
         case 4: pass1_last_stage<4>(sm, logG, logC, logM, c0, logNs, tw, Yt); break;
         case 3: pass1_last_stage<3>(sm, logG, logC, logM, c0, logNs, tw, Yt); break;
         case 2: pass1_last_stage<2>(sm, logG, logC, logM, c0, logNs, tw, Yt); break;
         default: pass1_last_stage<1>(sm, logG, logC, logM, c0, logNs, tw, Yt); break;
+    }
+}
+
+// ---- Pass 1, warp-specialised --------------------------------------------------------
+// The same column FFTs as k_pass1 (R-point FFTs over j1 of z[j1 C + j2] for G adjacent
+// columns j2, four-step twiddle, Y store), with the index map and gather taken off the
+// FFT warps: a persistent CTA holds kWsBufs tiles of 2^13 complex values in shared memory;
+// 16 producer warps compute Algorithm 1's indices and gather the samples of tile i + 1
+// (natural order, element g + G j1) while 16 consumer warps run the radix-16 Stockham
+// stages of tile i in the other buffer.  Hand-off by mbarriers: full[b] (every producer
+// thread arrives after its stores) and empty[b] (every consumer thread arrives after its
+// last reads).  Waits are bounded; on expiry the status word gets bit 1 and the CTA
+// leaves (the consumers decide together, by a barrier reduction, so none is left at a
+// named barrier).
+constexpr int kWsLogTile = 13;
+constexpr int kWsTile = 1 << kWsLogTile;
+constexpr int kWsBufStride = kWsTile + (kWsTile >> 4);  // padded float2 per buffer
+constexpr int kWsConsumers = 512;                       // 16 warps x 16 elements
+constexpr int kWsProducers = 512;                       // 16 warps
+constexpr int kWsThreads = kWsConsumers + kWsProducers;
+constexpr int kWsEPT = kWsTile / kWsConsumers;          // 16
+constexpr int kWsFine = 2048;                           // W_M^t, t < 2048, per CTA
+constexpr int kWsHeader = 128;                          // bytes: mbarriers
+constexpr int kWsBufs = 2;
+constexpr int kWsPUnroll = 4;                           // elements per producer batch
+static_assert(kWsEPT == 16, "one radix-16 butterfly per consumer thread and stage");
+static_assert(kWsTile % (kWsProducers * kWsPUnroll) == 0, "producer batches tile the buffer");
+
+size_t ws_pass1_smem()
+{
+    return (size_t)kWsHeader + (size_t)kWsBufs * kWsBufStride * sizeof(float2) + kWsFine * sizeof(float2);
+}
+
+// True (uniformly for the 512 consumer threads) when any of them passes true.
+__device__ __forceinline__ bool consumers_any(bool v)
+{
+    uint32_t r;
+    asm volatile(
+        "{\n .reg .pred p, q;\n setp.ne.u32 p, %1, 0;\n bar.red.or.pred q, 1, 512, p;\n"
+        " selp.u32 %0, 1, 0, q;\n}\n"
+        : "=r"(r)
+        : "r"((uint32_t)v)
+        : "memory");
+    return r != 0;
+}
+
+// W_M^t for t < M = 2^logM <= 2^24: W_{M / 2048}^{t div 2048} (the 8192-entry table) times
+// W_M^{t mod 2048} (the CTA's fine table).
+__device__ __forceinline__ float2 w_M(uint32_t t, int logM, const float2* __restrict__ tw,
+                                      const float2* fine)
+{
+    return cmul(__ldg(tw + ((t >> 11) << (24 - logM))), fine[t & (kWsFine - 1)]);
+}
+
+// Last column-FFT stage of the consumers: radix 2^LOGR_LAST with the stage twiddles, the
+// four-step twiddle W_M^{j2 k1} and the store of Y[k1][j2].
+template <int LOGR_LAST, int LG>
+__device__ __forceinline__ void ws_last_stage(const float2* __restrict__ sm, int logC, int logM,
+                                              int c0, int logNs, const float2* __restrict__ tw,
+                                              const float2* fine, float2* __restrict__ Yt, int tid)
+{
+    constexpr int RL = 1 << LOGR_LAST;
+    constexpr int BPT = kWsEPT / RL;
+    constexpr int G = 1 << LG;
+    const int Ns = 1 << logNs;
+    const int twshift = 13 - logNs - LOGR_LAST;
+    const uint32_t Mm = (uint32_t)((1 << logM) - 1);
+    // all of a thread's butterflies share the column j2 (kWsConsumers is a multiple of G)
+    const uint32_t j2 = (uint32_t)(c0 + (tid & (G - 1)));
+    // powers of W_M^{j2 Ns}: st[s] = (W_M^{j2 Ns})^s, at most four products deep
+    float2 st[RL];
+    st[0] = make_float2(1.f, 0.f);
+    st[1] = w_M((j2 * (uint32_t)Ns) & Mm, logM, tw, fine);
+#pragma unroll
+    for (int s = 2; s < RL; ++s) {
+        const int hb = (s & (s - 1)) == 0 ? (s >> 1) : (1 << (31 - __clz(s)));
+        st[s] = cmul(st[hb], st[s - hb]);
+    }
+#pragma unroll
+    for (int i = 0; i < BPT; ++i) {
+        const int b = tid + i * kWsConsumers;
+        const int g = b & (G - 1);
+        const int j = b >> LG;
+        float2 v[RL];
+#pragma unroll
+        for (int s = 0; s < RL; ++s) v[s] = sm[pad(g + G * (j + s * Ns))];
+        {
+            float2 w[RL];
+            w[1] = __ldg(tw + (j << twshift));
+#pragma unroll
+            for (int s = 2; s < RL; ++s) {
+                const int hb = (s & (s - 1)) == 0 ? (s >> 1) : (1 << (31 - __clz(s)));
+                w[s] = cmul(w[hb], w[s - hb]);
+            }
+#pragma unroll
+            for (int s = 1; s < RL; ++s) v[s] = cmul(v[s], w[s]);
+        }
+        Radix<LOGR_LAST>::dft(v);
+        const float2 u0 = w_M((j2 * (uint32_t)j) & Mm, logM, tw, fine);
+#pragma unroll
+        for (int s = 0; s < RL; ++s) {
+            const int k1 = j + s * Ns;
+            __stcs(Yt + ((int64_t)k1 << logC) + j2, cmul(v[Radix<LOGR_LAST>::out_pos(s)], cmul(u0, st[s])));
+        }
+    }
+}
+
+// Index map (FP32 fast path, compensated branch inside the guard band) and gather of the
+// two samples 2m, 2m + 1 of one complex element.
+__device__ __forceinline__ void ws_indices(const Anchor* __restrict__ at, int logB, int m,
+                                           int& i0, int& i1)
+{
+    const int ab = m >> logB;
+    const float4 a4 = __ldg(reinterpret_cast<const float4*>(at + ab));
+    const float q3 = __ldg(&at[ab].q3);
+    const int I = __float_as_int(a4.x) - kRoundBits;
+    const int d = m - ((ab << logB) + (1 << (logB - 1)));
+    unsigned bad = 0;
+    int id[2];
+#pragma unroll
+    for (int u = 0; u < 2; ++u) {
+        const float df = (float)(d + u);
+        const float xr = a4.y - df * fmaf(df, fmaf(df, q3, a4.w), a4.z);
+        const float y = __fadd_rn(xr, kRoundShift);
+        const float fr = __fsub_rn(xr, __fsub_rn(y, kRoundShift));
+        if (!(fabsf(fr) < 0.5f - kGuard)) bad |= 1u << u;
+        id[u] = m + u + I + __float_as_int(y);
+    }
+    if (bad) {
+        const Anchor a = at[ab];
+        if (bad & 1u) id[0] = m + a.I + off_round_precise(a, d);
+        if (bad & 2u) id[1] = m + 1 + a.I + off_round_precise(a, d + 1);
+    }
+    i0 = id[0];
+    i1 = id[1];
+}
+
+template <int LR, int LC>
+__global__ void __launch_bounds__(kWsThreads, 1) k_pass1_ws(SeriesView x, const Anchor* __restrict__ anc,
+                                                            Plan p, const float2* __restrict__ tw,
+                                                            float2* __restrict__ Y, int ntiles,
+                                                            unsigned long long* __restrict__ status)
+{
+    constexpr int LG = kWsLogTile - LR;  // columns per tile
+    constexpr int G = 1 << LG;
+    constexpr int LCG = LC - LG;        // log2 column groups (tiles) per template
+    constexpr int LM = LR + LC;
+    static_assert(LG >= 0 && LCG >= 0, "tile geometry");
+    extern __shared__ __align__(128) unsigned char wsm[];
+    uint64_t* full = reinterpret_cast<uint64_t*>(wsm);
+    uint64_t* empty = full + kWsBufs;
+    float2* bufs = reinterpret_cast<float2*>(wsm + kWsHeader);
+    float2* fine = bufs + kWsBufs * kWsBufStride;
+    if (threadIdx.x == 0) {
+#pragma unroll
+        for (int b = 0; b < kWsBufs; ++b) {
+            mbar_init(&full[b], kWsProducers);
+            mbar_init(&empty[b], kWsConsumers);
+        }
+    }
+    // fine twiddles W_M^t, t < 2048 (exact arguments t / 2^(LM - 1) of sincospi)
+    for (int t = threadIdx.x; t < kWsFine; t += kWsThreads) {
+        float sn, cs;
+        sincospif(ldexpf((float)t, 1 - LM), &sn, &cs);
+        fine[t] = make_float2(cs, -sn);
+    }
+    __syncthreads();
+    resolve_fill(x);
+    const int n = 2 << LM;
+    if (threadIdx.x >= kWsConsumers) {
+        // ---- producers: index map + gather of tile i into buffer i mod kWsBufs ----
+        const int pt = (int)threadIdx.x - kWsConsumers;
+        for (int i = 0;; ++i) {
+            const int u = (int)blockIdx.x + i * (int)gridDim.x;
+            if (u >= ntiles) break;
+            const int b = i % kWsBufs, k = i / kWsBufs;
+            if (k > 0 && !mbar_wait_parity(&empty[b], (uint32_t)((k - 1) & 1))) {
+                atomicOr(status, 2ull);
+                break;
+            }
+            const int tl = u >> LCG;
+            const int c0 = (u & ((1 << LCG) - 1)) << LG;
+            const Anchor* at = anc + (int64_t)tl * p.nanchor;
+            float2* sb = bufs + b * kWsBufStride;
+#pragma unroll 1
+            for (int e0 = 0; e0 < kWsTile; e0 += kWsProducers * kWsPUnroll) {
+                int id[2 * kWsPUnroll];
+#pragma unroll
+                for (int r = 0; r < kWsPUnroll; ++r) {
+                    const int e = e0 + pt + r * kWsProducers;
+                    const int m = 2 * (((e >> LG) << LC) + c0 + (e & (G - 1)));
+                    ws_indices(at, p.logB, m, id[2 * r], id[2 * r + 1]);
+                }
+                float2 v[kWsPUnroll];
+                if (x.f32) {
+#pragma unroll
+                    for (int r = 0; r < kWsPUnroll; ++r) v[r] = gather_pair_f32(x, n, id[2 * r], id[2 * r + 1]);
+                } else {
+                    unsigned short hv[2 * kWsPUnroll];
+                    float sv[2 * kWsPUnroll];
+#pragma unroll
+                    for (int q = 0; q < 2 * kWsPUnroll; ++q) {
+                        const bool in = (unsigned)id[q] < (unsigned)n;
+                        hv[q] = in ? __ldg(x.f16 + id[q]) : (unsigned short)0;
+                        sv[q] = !in ? 0.f : (x.uscale > 0.f ? x.uscale : __ldg(x.scale + (id[q] >> 12)));
+                    }
+#pragma unroll
+                    for (int r = 0; r < kWsPUnroll; ++r) {
+                        const bool in0 = (unsigned)id[2 * r] < (unsigned)n;
+                        const bool in1 = (unsigned)id[2 * r + 1] < (unsigned)n;
+                        v[r] = make_float2(in0 ? __half2float(__ushort_as_half(hv[2 * r])) * sv[2 * r] : x.fill,
+                                           in1 ? __half2float(__ushort_as_half(hv[2 * r + 1])) * sv[2 * r + 1] : x.fill);
+                    }
+                }
+#pragma unroll
+                for (int r = 0; r < kWsPUnroll; ++r) sb[pad(e0 + pt + r * kWsProducers)] = v[r];
+            }
+            mbar_arrive(&full[b]);
+        }
+        return;
+    }
+    // ---- consumers: column FFTs of tile i ----
+    const int ct = (int)threadIdx.x;
+    for (int i = 0;; ++i) {
+        const int u = (int)blockIdx.x + i * (int)gridDim.x;
+        if (u >= ntiles) break;
+        const int b = i % kWsBufs, k = i / kWsBufs;
+        const bool ok = mbar_wait_parity(&full[b], (uint32_t)(k & 1));
+        if (consumers_any(!ok)) {
+            if (ct == 0) atomicOr(status, 2ull);
+            break;
+        }
+        const int tl = u >> LCG;
+        const int c0 = (u & ((1 << LCG) - 1)) << LG;
+        float2* sb = bufs + b * kWsBufStride;
+        int logNs = 0;
+#pragma unroll
+        for (; logNs + 4 < LR; logNs += 4)
+            fft_stage<4, kWsEPT, true, SyncNamed<1, kWsConsumers>>(sb, LR, logNs, LG, 1, G, 0, tw, ct);
+        float2* Yt = Y + ((int64_t)tl << LM);
+        ws_last_stage<LR - ((LR - 1) / 4) * 4, LG>(sb, LC, LM, c0, ((LR - 1) / 4) * 4, tw, fine, Yt, ct);
+        mbar_arrive(&empty[b]);
     }
 }
 
@@ -462,11 +718,11 @@ __global__ void __launch_bounds__(1024, 1) k_pass2(const float2* __restrict__ Y,
     {
         int logNs = 4;
         for (; logNs + 4 <= logC; logNs += 4)
-            fft_stage<4, kEPT2, false>(sm, logC, logNs, logNP + 1, C, 1, skew, tw);
+            fft_stage<4, kEPT2, false>(sm, logC, logNs, logNP + 1, C, 1, skew, tw, threadIdx.x);
         const int rem = logC - logNs;
-        if (rem == 3) fft_stage<3, kEPT2, false>(sm, logC, logNs, logNP + 1, C, 1, skew, tw);
-        else if (rem == 2) fft_stage<2, kEPT2, false>(sm, logC, logNs, logNP + 1, C, 1, skew, tw);
-        else if (rem == 1) fft_stage<1, kEPT2, false>(sm, logC, logNs, logNP + 1, C, 1, skew, tw);
+        if (rem == 3) fft_stage<3, kEPT2, false>(sm, logC, logNs, logNP + 1, C, 1, skew, tw, threadIdx.x);
+        else if (rem == 2) fft_stage<2, kEPT2, false>(sm, logC, logNs, logNP + 1, C, 1, skew, tw, threadIdx.x);
+        else if (rem == 1) fft_stage<1, kEPT2, false>(sm, logC, logNs, logNP + 1, C, 1, skew, tw, threadIdx.x);
     }
     float* Pt = P + (int64_t)tl * M;
     if (p.ptrans) {
@@ -614,6 +870,10 @@ Pass2Fn pick_pass2(const Plan& p)
 
 }  // namespace
 
+namespace {
+cudaError_t ws_attributes(int* nsm);
+}
+
 // Large dynamic shared memory for the FFT passes, set once per device (a host-side
 // function attribute, so it is also safe to call while a stream is being captured).
 cudaError_t set_smem_attributes()
@@ -636,6 +896,8 @@ cudaError_t set_smem_attributes()
         e = cudaFuncSetAttribute(k_pass2<a, b, c>, cudaFuncAttributeMaxDynamicSharedMemorySize, bytes);
     BPS_PASS2_GEOMETRIES(BPS_ATTR)
 #undef BPS_ATTR
+    int nsm = 0;
+    if (e == cudaSuccess) e = ws_attributes(&nsm);
     if (e == cudaSuccess) done[dev] = true;
     return e;
 }
@@ -646,9 +908,63 @@ cudaError_t launch_twiddle_init(float2* tw, cudaStream_t s)
     return cudaGetLastError();
 }
 
-cudaError_t launch_pass1(const SeriesView& x, const Anchor* anc, int nt, const Plan& p,
-                         const float2* tw, float2* Y, cudaStream_t s)
+namespace {
+
+using WsFn = void (*)(SeriesView, const Anchor*, Plan, const float2*, float2*, int, unsigned long long*);
+
+// (log R, log C) of the warp-specialised pass 1: 2^20..2^24 complex points, R = 2^10..2^12
+#define BPS_WS_GEOMETRIES(X)                                                                          X(10, 10) X(11, 9) X(12, 8) X(10, 11) X(11, 10) X(12, 9) X(10, 12) X(11, 11) X(12, 10)            X(11, 12) X(12, 11) X(12, 12)
+
+WsFn pick_ws(const Plan& p)
 {
+#define BPS_PICK(a, b) \
+    if (p.logR == a && p.logC == b) return k_pass1_ws<a, b>;
+    BPS_WS_GEOMETRIES(BPS_PICK)
+#undef BPS_PICK
+    return nullptr;
+}
+
+cudaError_t ws_attributes(int* nsm)
+{
+    static std::mutex mu;
+    static int done[64] = {};
+    int dev = 0;
+    cudaError_t e = cudaGetDevice(&dev);
+    if (e != cudaSuccess) return e;
+    if (dev < 0 || dev >= 64) return cudaErrorInvalidDevice;
+    std::lock_guard<std::mutex> lk(mu);
+    if (!done[dev]) {
+        const int bytes = (int)ws_pass1_smem();
+#define BPS_ATTR(a, b) \
+    if (e == cudaSuccess) e = cudaFuncSetAttribute(k_pass1_ws<a, b>, cudaFuncAttributeMaxDynamicSharedMemorySize, bytes);
+        BPS_WS_GEOMETRIES(BPS_ATTR)
+#undef BPS_ATTR
+        int n = 0;
+        if (e == cudaSuccess) e = cudaDeviceGetAttribute(&n, cudaDevAttrMultiProcessorCount, dev);
+        if (e != cudaSuccess) return e;
+        done[dev] = n;
+    }
+    *nsm = done[dev];
+    return cudaSuccess;
+}
+
+}  // namespace
+
+cudaError_t launch_pass1(const SeriesView& x, const Anchor* anc, int nt, const Plan& p,
+                         const float2* tw, float2* Y, unsigned long long* status, cudaStream_t s)
+{
+    if (p.p1ws) {
+        const WsFn f = pick_ws(p);
+        if (!f || !status) return cudaErrorInvalidValue;
+        int nsm = 0;
+        cudaError_t e = ws_attributes(&nsm);
+        if (e != cudaSuccess) return e;
+        const int64_t ntiles = (int64_t)nt << (p.logC - (kWsLogTile - p.logR));
+        if (ntiles < 1 || ntiles > INT32_MAX) return cudaErrorInvalidValue;
+        const int grid = (int)std::min<int64_t>(ntiles, nsm);
+        f<<<grid, kWsThreads, ws_pass1_smem(), s>>>(x, anc, p, tw, Y, (int)ntiles, status);
+        return cudaGetLastError();
+    }
     const int logt = p.logR + p.logG;
     cudaError_t e = set_smem_attributes();
     if (e != cudaSuccess) return e;
