@@ -9,10 +9,11 @@ using namespace bps::rt;
 namespace bps {
 namespace rt {
 
-// Searches of a list of (series, bank) pairs captured into one CUDA graph: pairs are
-// spread over up to kGraphBranches parallel branches (fork/join events during the
-// capture); the pairs of one branch run in sequence and share its workspace.  Each pair
-// has its own candidate region (cap candidates) and counter.
+// Searches of a list of (series, bank) pairs captured into one CUDA graph: series too
+// large for four to share the L2 are searched one after another on one branch, then the
+// other pairs are spread over up to kGraphBranches parallel branches (fork/join events
+// during the capture); the pairs of one branch run in sequence and share its workspace.
+// Each pair has its own candidate region (cap candidates) and counter.
 constexpr int kGraphBranches = 4;
 
 struct GraphObj {
@@ -493,18 +494,35 @@ try {
     std::vector<Series*> ss((size_t)count);
     std::vector<Bank*> bb((size_t)count);
     std::vector<size_t> wsb((size_t)B, 0);
+    // L2-aware schedule: a series that a quarter of the L2 cannot hold is searched alone
+    // (phase A, one branch, in the order given), so its gathers stay in the L2 across the
+    // bank's templates; the smaller ones run on B parallel branches (phase B), each pair on
+    // the branch with the least work so far (templates x n log2 n)
+    int l2 = 0;
+    CK(cudaDeviceGetAttribute(&l2, cudaDevAttrL2CacheSize, ctx->device));
+    std::vector<int> branch((size_t)count, 0);
+    std::vector<char> big((size_t)count, 0);
+    std::vector<double> load((size_t)B, 0.0);
     for (int64_t i = 0; i < count; ++i) {
         int rc = lookup(ctx, series_ids[i], bank_ids[i], ss[i], bb[i]);
         if (rc) return rc;
         if ((rc = check_params(ctx, params, ss[i]->n))) return rc;
         Plan p;
         if ((rc = make_plan(ctx, *ss[i], *bb[i], *params, p))) return rc;
+        const size_t sbytes = (size_t)ss[i]->n * (ss[i]->dtype == BPS_F32 ? 4 : 2);
+        big[i] = (B > 1 && sbytes * 4 > (size_t)l2) ? 1 : 0;
+        if (!big[i]) {
+            const int bmin = (int)(std::min_element(load.begin(), load.end()) - load.begin());
+            branch[i] = bmin;
+            load[bmin] += (double)bb[i]->K * (double)ss[i]->n * (double)p.logn;
+        }
         int nt = params->batch > 0 ? (int)std::min<int64_t>(params->batch, bb[i]->K)
                                    : default_batch(p, bb[i]->K, params->mode);
         auto it = ctx->tuned.find(tune_key(p.logn, params->mode, p.lognh));
         if (params->batch == 0 && it != ctx->tuned.end()) nt = (int)std::min<int64_t>(it->second[2], bb[i]->K);
         const int64_t chunk = std::min<int64_t>((int64_t)nt * kAnchorChunk, bb[i]->K);
-        wsb[i % B] = std::max(wsb[i % B], ws_carve(p, nt, params->mode, (int)chunk, nullptr, nullptr));
+        size_t& w = wsb[branch[i]];
+        w = std::max(w, ws_carve(p, nt, params->mode, (int)chunk, nullptr, nullptr));
     }
     std::unique_ptr<GraphObj> g(new GraphObj());
     g->series.assign(series_ids, series_ids + count);
@@ -519,22 +537,30 @@ try {
     std::vector<cudaStream_t> br((size_t)B);
     CK(cudaStreamCreateWithFlags(&os, cudaStreamNonBlocking));
     for (auto& x : br) CK(cudaStreamCreateWithFlags(&x, cudaStreamNonBlocking));
-    cudaEvent_t fork;
+    cudaEvent_t fork, phase_a;
     std::vector<cudaEvent_t> join((size_t)B);
     CK(cudaEventCreateWithFlags(&fork, cudaEventDisableTiming));
+    CK(cudaEventCreateWithFlags(&phase_a, cudaEventDisableTiming));
     for (auto& e : join) CK(cudaEventCreateWithFlags(&e, cudaEventDisableTiming));
     int rc = BPS_OK;
     cudaError_t ce = cudaStreamBeginCapture(os, cudaStreamCaptureModeThreadLocal);
     if (ce == cudaSuccess) {
         cudaMemsetAsync(g->counts, 0, 2 * sizeof(unsigned long long) * count, os);
         cudaEventRecord(fork, os);
-        for (int b = 0; b < B; ++b) cudaStreamWaitEvent(br[b], fork, 0);
-        for (int64_t i = 0; i < count && !rc; ++i) {
+        cudaStreamWaitEvent(br[0], fork, 0);
+        auto capture_pair = [&](int64_t i) {
+            const int b = branch[i];
             Job job;
-            rc = job.setup(ctx, ss[i], bb[i], *params, br[i % B], g->cands + (size_t)i * g->cap,
-                           g->counts + 2 * i, g->cap, g->wsbuf[i % B], wsb[i % B]);
+            rc = job.setup(ctx, ss[i], bb[i], *params, br[b], g->cands + (size_t)i * g->cap,
+                           g->counts + 2 * i, g->cap, g->wsbuf[b], wsb[b]);
             while (!rc && !job.done()) rc = job.issue_batch();
-        }
+        };
+        for (int64_t i = 0; i < count && !rc; ++i)  // phase A: large series, one at a time
+            if (big[i]) capture_pair(i);
+        cudaEventRecord(phase_a, br[0]);
+        for (int b = 1; b < B; ++b) cudaStreamWaitEvent(br[b], phase_a, 0);
+        for (int64_t i = 0; i < count && !rc; ++i)  // phase B: the rest, B branches
+            if (!big[i]) capture_pair(i);
         for (int b = 0; b < B; ++b) {
             cudaEventRecord(join[b], br[b]);
             cudaStreamWaitEvent(os, join[b], 0);
@@ -543,6 +569,7 @@ try {
         if (ce == cudaSuccess && !rc) ce = cudaGraphInstantiate(&g->exec, g->graph, 0);
     }
     cudaEventDestroy(fork);
+    cudaEventDestroy(phase_a);
     for (auto e : join) cudaEventDestroy(e);
     for (auto x : br) cudaStreamDestroy(x);
     cudaStreamDestroy(os);

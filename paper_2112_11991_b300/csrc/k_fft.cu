@@ -423,74 +423,75 @@ constexpr int kWsConsumers = 512;                       // 16 warps x 16 element
 constexpr int kWsProducers = 512;                       // 16 warps
 constexpr int kWsThreads = kWsConsumers + kWsProducers;
 constexpr int kWsEPT = kWsTile / kWsConsumers;          // 16
-constexpr int kWsFine = 2048;                           // W_M^t, t < 2048, per CTA
+constexpr int kWsTw = 512;                              // stage twiddles held in smem
 constexpr int kWsHeader = 128;                          // bytes: mbarriers
 constexpr int kWsBufs = 2;
 constexpr int kWsPUnroll = 4;                           // elements per producer batch
+constexpr int kWsAnchors = 2048;                        // anchors of one template held in smem
 static_assert(kWsEPT == 16, "one radix-16 butterfly per consumer thread and stage");
 static_assert(kWsTile % (kWsProducers * kWsPUnroll) == 0, "producer batches tile the buffer");
 
 size_t ws_pass1_smem()
 {
-    return (size_t)kWsHeader + (size_t)kWsBufs * kWsBufStride * sizeof(float2) + kWsFine * sizeof(float2);
+    return (size_t)kWsHeader + (size_t)kWsBufs * kWsBufStride * sizeof(float2) + kWsTw * sizeof(float2) +
+           (size_t)kWsAnchors * (sizeof(float4) + sizeof(float));
 }
 
-// True (uniformly for the 512 consumer threads) when any of them passes true.
-__device__ __forceinline__ bool consumers_any(bool v)
+// True, for every one of the 512 threads of named barrier ID (1: consumers, 2: producers),
+// when any of them passes true; the threads wait in the barrier, and it orders their
+// memory accesses (what one thread acquired before it is visible to all after it).
+template <int ID>
+__device__ __forceinline__ bool group_any(bool v)
 {
     uint32_t r;
     asm volatile(
-        "{\n .reg .pred p, q;\n setp.ne.u32 p, %1, 0;\n bar.red.or.pred q, 1, 512, p;\n"
+        "{\n .reg .pred p, q;\n setp.ne.u32 p, %1, 0;\n bar.red.or.pred q, %2, 512, p;\n"
         " selp.u32 %0, 1, 0, q;\n}\n"
         : "=r"(r)
-        : "r"((uint32_t)v)
+        : "r"((uint32_t)v), "n"(ID)
         : "memory");
     return r != 0;
 }
 
-// W_M^t for t < M = 2^logM <= 2^24: W_{M / 2048}^{t div 2048} (the 8192-entry table) times
-// W_M^{t mod 2048} (the CTA's fine table).
-__device__ __forceinline__ float2 w_M(uint32_t t, int logM, const float2* __restrict__ tw,
-                                      const float2* fine)
-{
-    return cmul(__ldg(tw + ((t >> 11) << (24 - logM))), fine[t & (kWsFine - 1)]);
-}
-
-// Last column-FFT stage of the consumers: radix 2^LOGR_LAST with the stage twiddles, the
-// four-step twiddle W_M^{j2 k1} and the store of Y[k1][j2].
+// Last column-FFT stage of the consumers: radix 2^LOGR_LAST with the stage twiddles (from
+// the CTA's table stw: stw[j] = W_{Ns RL}^j, j < Ns), the four-step twiddle W_M^{j2 k1}
+// and the store of Y[k1][j2].
 template <int LOGR_LAST, int LG>
 __device__ __forceinline__ void ws_last_stage(const float2* __restrict__ sm, int logC, int logM,
-                                              int c0, int logNs, const float2* __restrict__ tw,
-                                              const float2* fine, float2* __restrict__ Yt, int tid)
+                                              int c0, int logNs, const float2* stw,
+                                              float2* __restrict__ Yt, int tid)
 {
     constexpr int RL = 1 << LOGR_LAST;
     constexpr int BPT = kWsEPT / RL;
     constexpr int G = 1 << LG;
     const int Ns = 1 << logNs;
-    const int twshift = 13 - logNs - LOGR_LAST;
     const uint32_t Mm = (uint32_t)((1 << logM) - 1);
     // all of a thread's butterflies share the column j2 (kWsConsumers is a multiple of G)
     const uint32_t j2 = (uint32_t)(c0 + (tid & (G - 1)));
     // powers of W_M^{j2 Ns}: st[s] = (W_M^{j2 Ns})^s, at most four products deep
     float2 st[RL];
     st[0] = make_float2(1.f, 0.f);
-    st[1] = w_M((j2 * (uint32_t)Ns) & Mm, logM, tw, fine);
+    st[1] = twiddle((j2 * (uint32_t)Ns) & Mm, logM);
 #pragma unroll
     for (int s = 2; s < RL; ++s) {
         const int hb = (s & (s - 1)) == 0 ? (s >> 1) : (1 << (31 - __clz(s)));
         st[s] = cmul(st[hb], st[s - hb]);
     }
+    // W_M^{j2 j} of the thread's butterflies: j steps by kWsConsumers / G
+    float2 u0 = twiddle((j2 * (uint32_t)(tid >> LG)) & Mm, logM), du;
+    if (BPT > 1) du = twiddle((j2 * (uint32_t)(kWsConsumers >> LG)) & Mm, logM);
 #pragma unroll
     for (int i = 0; i < BPT; ++i) {
         const int b = tid + i * kWsConsumers;
         const int g = b & (G - 1);
         const int j = b >> LG;
+        if (i > 0) u0 = cmul(u0, du);
         float2 v[RL];
 #pragma unroll
         for (int s = 0; s < RL; ++s) v[s] = sm[pad(g + G * (j + s * Ns))];
         {
             float2 w[RL];
-            w[1] = __ldg(tw + (j << twshift));
+            w[1] = stw[j];
 #pragma unroll
             for (int s = 2; s < RL; ++s) {
                 const int hb = (s & (s - 1)) == 0 ? (s >> 1) : (1 << (31 - __clz(s)));
@@ -500,7 +501,6 @@ __device__ __forceinline__ void ws_last_stage(const float2* __restrict__ sm, int
             for (int s = 1; s < RL; ++s) v[s] = cmul(v[s], w[s]);
         }
         Radix<LOGR_LAST>::dft(v);
-        const float2 u0 = w_M((j2 * (uint32_t)j) & Mm, logM, tw, fine);
 #pragma unroll
         for (int s = 0; s < RL; ++s) {
             const int k1 = j + s * Ns;
@@ -509,14 +509,48 @@ __device__ __forceinline__ void ws_last_stage(const float2* __restrict__ sm, int
     }
 }
 
+// A middle radix-16 Stockham stage of the consumers (Ns = 2^logNs > 1, one butterfly per
+// thread), stage twiddles from the CTA's table stw: stw[k] = W_{16 Ns}^k, k < Ns.
+template <int LG>
+__device__ __forceinline__ void ws_mid_stage(float2* buf, int logR, int logNs, const float2* stw, int tid)
+{
+    constexpr int G = 1 << LG;
+    const int logQ = logR - 4;
+    const int Ns = 1 << logNs;
+    const int line = tid & (G - 1);
+    const int j = tid >> LG;
+    const int k = j & (Ns - 1);
+    float2 v[16];
+#pragma unroll
+    for (int s = 0; s < 16; ++s) v[s] = buf[pad(line + G * (j + (s << logQ)))];
+    {
+        float2 w[16];
+        w[1] = stw[k];
+#pragma unroll
+        for (int s = 2; s < 16; ++s) {
+            const int hb = (s & (s - 1)) == 0 ? (s >> 1) : (1 << (31 - __clz(s)));
+            w[s] = cmul(w[hb], w[s - hb]);
+        }
+#pragma unroll
+        for (int s = 1; s < 16; ++s) v[s] = cmul(v[s], w[s]);
+    }
+    const int dst = line + G * (((j >> logNs) << (logNs + 4)) + k);
+    SyncNamed<1, kWsConsumers>::sync();
+    Radix<4>::dft(v);
+#pragma unroll
+    for (int s = 0; s < 16; ++s) buf[pad(dst + G * s * Ns)] = v[Radix<4>::out_pos(s)];
+    SyncNamed<1, kWsConsumers>::sync();
+}
+
 // Index map (FP32 fast path, compensated branch inside the guard band) and gather of the
 // two samples 2m, 2m + 1 of one complex element.
-__device__ __forceinline__ void ws_indices(const Anchor* __restrict__ at, int logB, int m,
-                                           int& i0, int& i1)
+__device__ __forceinline__ void ws_indices(const Anchor* __restrict__ at, const float4* a4c,
+                                           const float* q3c, int logB, int m, int& i0, int& i1)
 {
     const int ab = m >> logB;
-    const float4 a4 = __ldg(reinterpret_cast<const float4*>(at + ab));
-    const float q3 = __ldg(&at[ab].q3);
+    // fast-path fields from the CTA's copy of the template's anchors when it holds them
+    const float4 a4 = a4c ? a4c[ab] : __ldg(reinterpret_cast<const float4*>(at + ab));
+    const float q3 = a4c ? q3c[ab] : __ldg(&at[ab].q3);
     const int I = __float_as_int(a4.x) - kRoundBits;
     const int d = m - ((ab << logB) + (1 << (logB - 1)));
     unsigned bad = 0;
@@ -554,38 +588,74 @@ __global__ void __launch_bounds__(kWsThreads, 1) k_pass1_ws(SeriesView x, const 
     uint64_t* full = reinterpret_cast<uint64_t*>(wsm);
     uint64_t* empty = full + kWsBufs;
     float2* bufs = reinterpret_cast<float2*>(wsm + kWsHeader);
-    float2* fine = bufs + kWsBufs * kWsBufStride;
+    float2* stw = bufs + kWsBufs * kWsBufStride;  // [0, 16): W_256^k; [16, 16 + Ns_last): last stage
+    float4* a4s = reinterpret_cast<float4*>(stw + kWsTw);
+    float* q3s = reinterpret_cast<float*>(a4s + kWsAnchors);
     if (threadIdx.x == 0) {
 #pragma unroll
         for (int b = 0; b < kWsBufs; ++b) {
             mbar_init(&full[b], kWsProducers);
-            mbar_init(&empty[b], kWsConsumers);
+            mbar_init(&empty[b], kWsConsumers / 32);
         }
     }
-    // fine twiddles W_M^t, t < 2048 (exact arguments t / 2^(LM - 1) of sincospi)
-    for (int t = threadIdx.x; t < kWsFine; t += kWsThreads) {
-        float sn, cs;
-        sincospif(ldexpf((float)t, 1 - LM), &sn, &cs);
-        fine[t] = make_float2(cs, -sn);
-    }
+    // stage twiddles from the 8192 table: W_256^k, k < 16, for the one middle radix-16
+    // stage (Ns = 16), and W_{Ns RL}^j, j < Ns = 256, for the last stage (radix RL = R / 256)
+    constexpr int LNS_LAST = ((LR - 1) / 4) * 4;
+    constexpr int RL_LAST = LR - LNS_LAST;
+    static_assert(LNS_LAST == 8 && 16 + (1 << LNS_LAST) <= kWsTw, "stages 16 x 16 x (R / 256)");
+    for (int t = threadIdx.x; t < 16; t += kWsThreads) stw[t] = __ldg(tw + (t << (13 - 8)));
+    for (int t = threadIdx.x; t < (1 << LNS_LAST); t += kWsThreads)
+        stw[16 + t] = __ldg(tw + (t << (13 - LNS_LAST - RL_LAST)));
     __syncthreads();
     resolve_fill(x);
     const int n = 2 << LM;
     if (threadIdx.x >= kWsConsumers) {
         // ---- producers: index map + gather of tile i into buffer i mod kWsBufs ----
         const int pt = (int)threadIdx.x - kWsConsumers;
+        const bool cache = p.nanchor <= kWsAnchors;
+        int cached = -1;  // template whose anchors the CTA holds
         for (int i = 0;; ++i) {
             const int u = (int)blockIdx.x + i * (int)gridDim.x;
             if (u >= ntiles) break;
             const int b = i % kWsBufs, k = i / kWsBufs;
-            if (k > 0 && !mbar_wait_parity(&empty[b], (uint32_t)((k - 1) & 1))) {
-                atomicOr(status, 2ull);
+            // one producer polls for the buffer to be free, the others wait in the barrier
+            bool ok = true;
+            if (k > 0 && pt == 0) ok = mbar_wait_parity(&empty[b], (uint32_t)((k - 1) & 1));
+            if (group_any<2>(!ok)) {
+                if (pt == 0) atomicOr(status, 2ull);
                 break;
             }
             const int tl = u >> LCG;
             const int c0 = (u & ((1 << LCG) - 1)) << LG;
             const Anchor* at = anc + (int64_t)tl * p.nanchor;
+            if (cache && tl != cached) {  // every producer is past the previous tile here
+                for (int a = pt; a < (int)p.nanchor; a += kWsProducers) {
+                    a4s[a] = __ldg(reinterpret_cast<const float4*>(at + a));
+                    q3s[a] = __ldg(&at[a].q3);
+                }
+                asm volatile("bar.sync 2, 512;" ::: "memory");
+                cached = tl;
+            }
+            const float4* a4c = cache ? a4s : nullptr;
             float2* sb = bufs + b * kWsBufStride;
+            if (x.f32 && x.fillp) {
+                // FP32 series: every sample of the tile by a 4-byte asynchronous copy (the
+                // series mean from its device copy outside [0, n)), so all 32 of the
+                // thread's gathers are in flight at once; the mbarrier counts the thread's
+                // arrival when they have landed
+#pragma unroll 4
+                for (int r = 0; r < kWsTile / kWsProducers; ++r) {
+                    const int e = pt + r * kWsProducers;
+                    const int m = 2 * (((e >> LG) << LC) + c0 + (e & (G - 1)));
+                    int i0, i1;
+                    ws_indices(at, a4c, q3s, p.logB, m, i0, i1);
+                    const uint32_t dst = smem_u32(sb + pad(e));
+                    cp_async4(dst, (unsigned)i0 < (unsigned)n ? x.f32 + i0 : x.fillp);
+                    cp_async4(dst + 4u, (unsigned)i1 < (unsigned)n ? x.f32 + i1 : x.fillp);
+                }
+                cp_async_mbar_arrive(&full[b]);
+                continue;
+            }
 #pragma unroll 1
             for (int e0 = 0; e0 < kWsTile; e0 += kWsProducers * kWsPUnroll) {
                 int id[2 * kWsPUnroll];
@@ -593,7 +663,7 @@ __global__ void __launch_bounds__(kWsThreads, 1) k_pass1_ws(SeriesView x, const 
                 for (int r = 0; r < kWsPUnroll; ++r) {
                     const int e = e0 + pt + r * kWsProducers;
                     const int m = 2 * (((e >> LG) << LC) + c0 + (e & (G - 1)));
-                    ws_indices(at, p.logB, m, id[2 * r], id[2 * r + 1]);
+                    ws_indices(at, a4c, q3s, p.logB, m, id[2 * r], id[2 * r + 1]);
                 }
                 float2 v[kWsPUnroll];
                 if (x.f32) {
@@ -621,6 +691,9 @@ __global__ void __launch_bounds__(kWsThreads, 1) k_pass1_ws(SeriesView x, const 
             }
             mbar_arrive(&full[b]);
         }
+        // the thread's asynchronous copies land before it leaves (the CTA's shared memory
+        // outlives them also when the consumers gave up on a wait)
+        asm volatile("cp.async.wait_all;" ::: "memory");
         return;
     }
     // ---- consumers: column FFTs of tile i ----
@@ -629,21 +702,23 @@ __global__ void __launch_bounds__(kWsThreads, 1) k_pass1_ws(SeriesView x, const 
         const int u = (int)blockIdx.x + i * (int)gridDim.x;
         if (u >= ntiles) break;
         const int b = i % kWsBufs, k = i / kWsBufs;
-        const bool ok = mbar_wait_parity(&full[b], (uint32_t)(k & 1));
-        if (consumers_any(!ok)) {
+        // one consumer polls for the tile, the others wait in the barrier
+        bool ok = true;
+        if (ct == 0) ok = mbar_wait_parity(&full[b], (uint32_t)(k & 1));
+        if (group_any<1>(!ok)) {
             if (ct == 0) atomicOr(status, 2ull);
             break;
         }
         const int tl = u >> LCG;
         const int c0 = (u & ((1 << LCG) - 1)) << LG;
         float2* sb = bufs + b * kWsBufStride;
-        int logNs = 0;
+        fft_stage<4, kWsEPT, true, SyncNamed<1, kWsConsumers>>(sb, LR, 0, LG, 1, G, 0, tw, ct);
 #pragma unroll
-        for (; logNs + 4 < LR; logNs += 4)
-            fft_stage<4, kWsEPT, true, SyncNamed<1, kWsConsumers>>(sb, LR, logNs, LG, 1, G, 0, tw, ct);
+        for (int logNs = 4; logNs < LNS_LAST; logNs += 4) ws_mid_stage<LG>(sb, LR, logNs, stw, ct);
         float2* Yt = Y + ((int64_t)tl << LM);
-        ws_last_stage<LR - ((LR - 1) / 4) * 4, LG>(sb, LC, LM, c0, ((LR - 1) / 4) * 4, tw, fine, Yt, ct);
-        mbar_arrive(&empty[b]);
+        ws_last_stage<RL_LAST, LG>(sb, LC, LM, c0, LNS_LAST, stw + 16, Yt, ct);
+        __syncwarp();
+        if ((ct & 31) == 0) mbar_arrive(&empty[b]);  // the warp's reads of the buffer are done
     }
 }
 

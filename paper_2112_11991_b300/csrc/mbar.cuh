@@ -60,6 +60,19 @@ __device__ __forceinline__ bool mbar_wait_parity(uint64_t* bar, uint32_t parity,
     return false;
 }
 
+// 4-byte asynchronous copy global -> shared through the L1 (both addresses 4-byte aligned)
+__device__ __forceinline__ void cp_async4(uint32_t dst, const void* src)
+{
+    asm volatile("cp.async.ca.shared.global [%0], [%1], 4;" ::"r"(dst), "l"(src) : "memory");
+}
+
+// One arrival on the mbarrier once every cp.async this thread issued before has landed
+// (counts as one of the barrier's expected arrivals).
+__device__ __forceinline__ void cp_async_mbar_arrive(uint64_t* bar)
+{
+    asm volatile("cp.async.mbarrier.arrive.noinc.shared::cta.b64 [%0];" ::"r"(smem_u32(bar)) : "memory");
+}
+
 // Arrive on an mbarrier (release; one arrival).
 __device__ __forceinline__ void mbar_arrive(uint64_t* bar)
 {
