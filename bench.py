@@ -58,6 +58,8 @@ def parse():
                     help="log2 of the four-step row length C (0 = library / autotuner)")
     ap.add_argument("--pass1-kind", type=int, default=0,
                     help="0 = library / autotuner, 1 = one-phase pass 1, 2 = warp-specialised")
+    ap.add_argument("--pass2-kind", type=int, default=0,
+                    help="0 = library / autotuner, 1 = one-phase pass 2, 2 = TMA-fed")
     ap.add_argument("--power-layout", type=int, default=0,
                     help="0 = library / autotuner, 1 = bin order, 2 = row-major blocks")
     ap.add_argument("--dtype", default="f32", choices=["f32", "f16"],
@@ -497,11 +499,12 @@ def main():
     # launch shapes of the fused form chosen by the library's autotuner on 64 templates
     tuned = None
     if (args.batch == 0 and args.log_tile == 0 and args.log_tile2 == 0 and args.log_cols == 0
-            and args.pass1_kind == 0 and args.power_layout == 0):
+            and args.pass1_kind == 0 and args.pass2_kind == 0 and args.power_layout == 0):
         best, ms_t = ctx.autotune(sid, bid, bps.default_params(cand_cap=CAND_CAP),
                                   sample_templates=min(64, K))
         tuned = {"log_tile": best.log_tile, "log_tile2": best.log_tile2, "batch": best.batch,
                  "log_cols": best.log_cols, "pass1_kind": best.pass1_kind,
+                 "pass2_kind": best.pass2_kind,
                  "power_layout": best.power_layout,
                  "ms_per_template_sample": ms_t}
 
@@ -511,6 +514,7 @@ def main():
                                  log_tile2=args.log_tile2,
                                  log_cols=args.log_cols if mode == 0 else 0,
                                  pass1_kind=args.pass1_kind if mode == 0 else 0,
+                                 pass2_kind=args.pass2_kind if mode == 0 else 0,
                                  power_layout=args.power_layout if mode == 0 else 0)
         ctx.set_profiling(False)
         for _ in range(warmup):
@@ -583,7 +587,8 @@ def main():
     d2h = 0
     prm = bps.default_params(batch=args.batch, cand_cap=CAND_CAP, log_tile=args.log_tile,
                              log_tile2=args.log_tile2, log_cols=args.log_cols,
-                             pass1_kind=args.pass1_kind, power_layout=args.power_layout)
+                             pass1_kind=args.pass1_kind, pass2_kind=args.pass2_kind,
+                             power_layout=args.power_layout)
     for i in range(args.warmup + args.steps):
         torch.cuda.synchronize(dev)
         t0 = time.perf_counter()

@@ -101,7 +101,17 @@ typedef struct {
                            /* is organised; 0 = library's choice                        */
     int32_t power_layout;  /* BPS_POWER_*: how pass 2 stores the power spectrum;        */
                            /* 0 = library's choice                                      */
+    int32_t pass2_kind;    /* BPS_PASS2_*: how pass 2 (row FFTs + split + power) gets    */
+                           /* its rows; 0 = library's choice                            */
 } bps_search_params;
+
+/* bps_search_params.pass2_kind */
+#define BPS_PASS2_AUTO      0  /* the autotuned choice, else the one-phase kernel            */
+#define BPS_PASS2_FUSED     1  /* each CTA loads its rows into registers for the first stage */
+#define BPS_PASS2_TMA       2  /* persistent CTAs: one thread copies the next tile's rows    */
+                               /* into a staging buffer with TMA bulk copies while 16 warps  */
+                               /* transform the current one (2^13-complex tiles, R and C in  */
+                               /* 2^10..2^12, else INVALID_ARG)                               */
 
 /* bps_search_params.pass1_kind */
 #define BPS_PASS1_AUTO      0  /* the autotuned choice, else the one-phase kernel            */

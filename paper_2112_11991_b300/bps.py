@@ -38,6 +38,9 @@ BPS_PASS1_WARPSPEC = 2
 BPS_POWER_AUTO = 0
 BPS_POWER_BINS = 1
 BPS_POWER_ROWS = 2
+BPS_PASS2_AUTO = 0
+BPS_PASS2_FUSED = 1
+BPS_PASS2_TMA = 2
 
 EXPORTED = ["bps_default_params", "bps_create", "bps_destroy", "bps_load_series",
             "bps_load_bank", "bps_search", "bps_query", "bps_fetch_candidates",
@@ -82,7 +85,7 @@ class bps_search_params(C.Structure):
                 ("auto_thr", C.c_int32), ("mode", C.c_int32), ("cand_cap", C.c_int64),
                 ("precision", C.c_int32), ("batch", C.c_int32), ("log_tile", C.c_int32),
                 ("log_tile2", C.c_int32), ("log_cols", C.c_int32), ("pass1_kind", C.c_int32),
-                ("power_layout", C.c_int32)]
+                ("power_layout", C.c_int32), ("pass2_kind", C.c_int32)]
 
 
 class bps_server_config(C.Structure):

@@ -685,17 +685,24 @@ try {
     if (base->pass1_kind != BPS_PASS1_WARPSPEC)
         for (int t : tiles) p1.push_back({BPS_PASS1_FUSED, t});
     if (base->mode == BPS_MODE_FUSED && base->pass1_kind != BPS_PASS1_FUSED) p1.push_back({BPS_PASS1_WARPSPEC, 13});
+    // pass 2: the one-phase kernel at both tiles, and the TMA-fed one (2^13 tiles) where built
+    std::vector<std::pair<int, int>> p2;  // (kind, tile)
+    if (base->pass2_kind != BPS_PASS2_TMA)
+        for (int t : tiles) p2.push_back({BPS_PASS2_FUSED, t});
+    if (base->mode == BPS_MODE_FUSED && base->pass2_kind != BPS_PASS2_FUSED) p2.push_back({BPS_PASS2_TMA, 13});
     for (int lc : splits)
     for (auto k1 : p1)
-        for (int t2 : tiles)
+        for (auto k2 : p2)
             for (int nb : batches) {
                 if (nb > sub.K) continue;
                 const int lcx = lc ? lc : default_log_cols(logM);
                 if (k1.first == BPS_PASS1_WARPSPEC && !ws_pass1_built(logM - lcx, lcx)) continue;
+                if (k2.first == BPS_PASS2_TMA && !tma_pass2_built(logM - lcx, lcx, 13)) continue;
                 bps_search_params pr = *base;
                 pr.pass1_kind = k1.first;
                 pr.log_tile = k1.second;
-                pr.log_tile2 = t2;
+                pr.pass2_kind = k2.first;
+                pr.log_tile2 = k2.second;
                 pr.log_cols = lc;
                 pr.batch = nb;
                 double ms_best = 1e30;
@@ -724,7 +731,7 @@ try {
     cudaFree(cnt);
     if (rc) return rc;
     ctx->tuned[tune_key(ilog2(s->n), base->mode, ilog2(base->nharm_max))] = {
-        bp.log_tile, bp.log_tile2, bp.batch, bp.log_cols, bp.pass1_kind, bp.power_layout};
+        bp.log_tile, bp.log_tile2, bp.batch, bp.log_cols, bp.pass1_kind, bp.power_layout, bp.pass2_kind};
     *best = bp;
     if (best_ms_per_template) *best_ms_per_template = best_ms / (double)sub.K;
     return BPS_OK;

@@ -60,6 +60,7 @@ struct Plan {
     int ptrans;     // 1: pass 2 writes the power row-major by k1, P'[k1 C + k2] for bin
                     // k1 + R k2, and the median kernel transposes it into bin order
     int p1ws;       // 1: warp-specialised pass 1 (producer warps gather, consumer warps FFT)
+    int p2tma;      // 1: pass 2 fed by TMA bulk copies of its rows (persistent, 2^13 tiles)
     double tsamp;
 };
 
@@ -104,6 +105,13 @@ inline void plan_geometry(Plan& p, int logTile = 14, int logTile2 = 13, int logC
     if (p.logNP < 0) p.logNP = 0;
     p.ptrans = 0;
     p.p1ws = 0;
+    p.p2tma = 0;
+}
+
+// Four-step splits the TMA-fed pass 2 is built for (2^13-complex tiles).
+inline bool tma_pass2_built(int logR, int logC, int logTile2)
+{
+    return logTile2 == 13 && logR >= 10 && logR <= 12 && logC >= 10 && logC <= 12;
 }
 
 // Anchor block length B = 2^logB: the largest (<= 2^14, <= n) for which every
@@ -169,8 +177,9 @@ cudaError_t launch_wait_selftest(int limit, unsigned long long* status, cudaStre
 // its bounded mbarrier waits expired (unused by the one-phase form)
 cudaError_t launch_pass1(const SeriesView& x, const Anchor* anc, int nt, const Plan& p,
                          const float2* tw, float2* Y, unsigned long long* status, cudaStream_t s);
+// status: as launch_pass1 (the TMA-fed form sets bit 2 when a bounded wait expired)
 cudaError_t launch_pass2(const float2* Y, int nt, const Plan& p, const float2* tw,
-                         float* P, cudaStream_t s);
+                         float* P, unsigned long long* status, cudaStream_t s);
 cudaError_t launch_power_from_r2c(const float2* X, int nt, const Plan& p, float* P,
                                   cudaStream_t s);
 // Lower median of each block of W bins and whitening into P (bin order; scale receives

@@ -163,7 +163,7 @@ try {
     if (cudaGetLastError() != cudaSuccess) return BPS_ERR_CUDA;
     if (launch_anchors(dt, 0, 1, p, anc, st) != cudaSuccess) return BPS_ERR_CUDA;
     if (launch_pass1(v, anc, 1, p, tw, Y, nullptr, st) != cudaSuccess) return BPS_ERR_CUDA;
-    if (launch_pass2(Y, 1, p, tw, P, st) != cudaSuccess) return BPS_ERR_CUDA;
+    if (launch_pass2(Y, 1, p, tw, P, nullptr, st) != cudaSuccess) return BPS_ERR_CUDA;
     if (launch_block_median(P, 1, p, scale, st) != cudaSuccess) return BPS_ERR_CUDA;
     if (launch_whitened(P, scale, 1, p, d_pw_out, st) != cudaSuccess) return BPS_ERR_CUDA;
     return BPS_OK;

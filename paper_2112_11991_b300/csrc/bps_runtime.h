@@ -89,8 +89,8 @@ struct bps_ctx {
     float2* tw = nullptr;
     bool profiling = false;
     // autotuned launch shapes per (log2 n, mode, log2 nharm): tile1, tile2, batch, log C,
-    // pass-1 kind, power layout
-    std::map<int, std::array<int, 6>> tuned;
+    // pass-1 kind, power layout, pass-2 kind
+    std::map<int, std::array<int, 7>> tuned;
     std::map<int64_t, bps::rt::GraphObj*> graphs;
 };
 
@@ -188,6 +188,8 @@ inline int check_params(bps_ctx* ctx, const bps_search_params* pr, int64_t n)
         return fail(ctx, BPS_ERR_INVALID_ARG, "unknown pass1_kind %d", pr->pass1_kind);
     if (pr->power_layout < BPS_POWER_AUTO || pr->power_layout > BPS_POWER_ROWS)
         return fail(ctx, BPS_ERR_INVALID_ARG, "unknown power_layout %d", pr->power_layout);
+    if (pr->pass2_kind < BPS_PASS2_AUTO || pr->pass2_kind > BPS_PASS2_TMA)
+        return fail(ctx, BPS_ERR_INVALID_ARG, "unknown pass2_kind %d", pr->pass2_kind);
     return BPS_OK;
 }
 
@@ -215,7 +217,7 @@ inline int make_plan(bps_ctx* ctx, const Series& s, const Bank& b, const bps_sea
     p.logn = ilog2(s.n);
     p.M = s.n / 2;
     p.logM = p.logn - 1;
-    int t1 = 14, t2 = 13, lc = 0, p1k = BPS_PASS1_FUSED, pl = BPS_POWER_AUTO;
+    int t1 = 14, t2 = 13, lc = 0, p1k = BPS_PASS1_FUSED, pl = BPS_POWER_AUTO, p2k = BPS_PASS2_FUSED;
     bool tuned = false;
     if (ctx) {
         auto it = ctx->tuned.find(tune_key(ilog2(s.n), pr.mode, ilog2(pr.nharm_max)));
@@ -225,6 +227,7 @@ inline int make_plan(bps_ctx* ctx, const Series& s, const Bank& b, const bps_sea
             lc = it->second[3];
             p1k = it->second[4];
             pl = it->second[5];
+            p2k = it->second[6];
             tuned = true;
         }
     }
@@ -244,6 +247,19 @@ inline int make_plan(bps_ctx* ctx, const Series& s, const Bank& b, const bps_sea
                             p.logR, p.logC);
         } else {
             p.p1ws = 1;
+        }
+    }
+    // pass-2 organisation, chosen like pass 1's
+    int kind2 = pr.pass2_kind;
+    if (kind2 == BPS_PASS2_AUTO)
+        kind2 = (tuned && !pr.log_cols && !pr.log_tile2) ? p2k : BPS_PASS2_FUSED;
+    if (pr.mode == BPS_MODE_FUSED && kind2 == BPS_PASS2_TMA) {
+        if (!tma_pass2_built(p.logR, p.logC, p.logTile2)) {
+            if (pr.pass2_kind == BPS_PASS2_TMA)
+                return fail(ctx, BPS_ERR_INVALID_ARG,
+                            "the TMA-fed pass 2 is built for 2^13 tiles and R, C in 2^10..2^12");
+        } else {
+            p.p2tma = 1;
         }
     }
     // row-major power (in groups of NP rows) when a pass-2 CTA holds at most two row pairs,
@@ -447,7 +463,7 @@ inline int run_spectrum(bps_ctx* ctx, const Series& s, const Bank& b, const Plan
         CK(launch_pass1(v, anc, nt, p, ctx->tw, w.Y, status, st));
         tm.end();
         tm.begin(BPS_STAGE_PASS2);
-        CK(launch_pass2(w.Y, nt, p, ctx->tw, p.ptrans ? w.Pt : w.P, st));
+        CK(launch_pass2(w.Y, nt, p, ctx->tw, p.ptrans ? w.Pt : w.P, status, st));
         tm.end();
     } else {
         cufftHandle h;

@@ -740,13 +740,15 @@ __device__ __forceinline__ void power_pair(float2 zk, float2 zm, float2 w, float
 // the self-mirrored rows 0 and R/2), then real-FFT split and power.  Items are
 // assigned q-fastest so each warp writes NP consecutive bins per k2.
 // LR, LC, LNP >= 0: log R, log C, log NP fixed at compile time; -1: from the plan.
-template <int LR, int LC, int LNP>
-__global__ void __launch_bounds__(1024, 1) k_pass2(const float2* __restrict__ Y, Plan p,
-                                                  const float2* __restrict__ tw,
-                                                  float* __restrict__ P)
+// One pass-2 tile (template tl, row pairs from q0) by the tid-th of nthr threads: the
+// first radix-16 stage reads the rows from Y in global memory (STAGED = false) or from the
+// unpadded copy of the tile's 2 NP rows in shared memory at src, line l at src + l C
+// (STAGED = true); the tile is transformed in sm; SYNC is the barrier of the nthr threads.
+template <int LR, int LC, int LNP, class SYNC, bool STAGED>
+__device__ __forceinline__ void pass2_tile(const float2* __restrict__ src, int tl, int q0, const Plan& p,
+                                           const float2* __restrict__ tw, float* __restrict__ P,
+                                           float2* sm, float2* s_wq, int tid)
 {
-    extern __shared__ float2 sm[];
-    const int tl = blockIdx.y;
     const int logR = LR >= 0 ? LR : p.logR;
     const int logC = LC >= 0 ? LC : p.logC;
     const int logM = logR + logC;
@@ -755,9 +757,8 @@ __global__ void __launch_bounds__(1024, 1) k_pass2(const float2* __restrict__ Y,
     const int R = 1 << logR, C = 1 << logC;
     const int logNP = LNP >= 0 ? LNP : p.logNP;
     const int NP = 1 << logNP;
-    const int q0 = blockIdx.x << logNP;
-    const int nthr = (NP * C * 2) / kEPT2;  // == blockDim.x
-    const float2* Yt = Y + (int64_t)tl * M;
+    const int nthr = (NP * C * 2) / kEPT2;  // threads of the tile
+    const float2* Yt = src + (STAGED ? 0 : (int64_t)tl * M);
     // lines [0, NP): low rows q0 + l ; lines [NP, 2NP): their mirrors.  Line l starts
     // at pad(l*C) + l*skew (pad(l*C) is a multiple of 16 complex).  In the split phase a
     // half-warp reads NP lines at 16/NP consecutive k2 each; skew = 16/NP puts the lines
@@ -767,37 +768,41 @@ __global__ void __launch_bounds__(1024, 1) k_pass2(const float2* __restrict__ Y,
     const int skew = logNP <= 4 ? (16 >> logNP) : (logNP == 5 ? 1 : 0);
     // W_N^q of the NP low rows, for the row-major power layout (plan.ptrans, NP <= 2);
     // visible to all after the first-stage barrier
-    __shared__ float2 s_wq[64];
-    if (p.ptrans && (int)threadIdx.x < NP)
-        s_wq[threadIdx.x] = twiddle((uint32_t)(q0 + threadIdx.x), logn);
+    if (p.ptrans && tid < NP) s_wq[tid] = twiddle((uint32_t)(q0 + tid), logn);
     const int logQ = logC - 4;
     constexpr int BPT1 = kEPT2 / 16;
 #pragma unroll
     for (int i = 0; i < BPT1; ++i) {
-        const int b = threadIdx.x + i * nthr;
+        const int b = tid + i * nthr;
         const int j = b & ((1 << logQ) - 1);
         const int line = b >> logQ;
         const int q = q0 + (line & (NP - 1));
         const int row = (line < NP) ? q : (q == 0 ? (R >> 1) : R - q);
-        const float2* src = Yt + ((int64_t)row << logC) + j;
         float2 v[16];
+        if (STAGED) {
+            const float2* rs = Yt + ((int64_t)line << logC) + j;
 #pragma unroll
-        for (int s = 0; s < 16; ++s) v[s] = __ldg(src + (s << logQ));
+            for (int s = 0; s < 16; ++s) v[s] = rs[s << logQ];
+        } else {
+            const float2* rs = Yt + ((int64_t)row << logC) + j;
+#pragma unroll
+            for (int s = 0; s < 16; ++s) v[s] = __ldg(rs + (s << logQ));
+        }
         Radix<4>::dft(v);
         const int base = line * C + 16 * j;
         const int lsk = line * skew;
 #pragma unroll
         for (int s = 0; s < 16; ++s) sm[pad(base + s) + lsk] = v[Radix<4>::out_pos(s)];
     }
-    __syncthreads();
+    SYNC::sync();
     {
         int logNs = 4;
         for (; logNs + 4 <= logC; logNs += 4)
-            fft_stage<4, kEPT2, false>(sm, logC, logNs, logNP + 1, C, 1, skew, tw, threadIdx.x);
+            fft_stage<4, kEPT2, false, SYNC>(sm, logC, logNs, logNP + 1, C, 1, skew, tw, tid);
         const int rem = logC - logNs;
-        if (rem == 3) fft_stage<3, kEPT2, false>(sm, logC, logNs, logNP + 1, C, 1, skew, tw, threadIdx.x);
-        else if (rem == 2) fft_stage<2, kEPT2, false>(sm, logC, logNs, logNP + 1, C, 1, skew, tw, threadIdx.x);
-        else if (rem == 1) fft_stage<1, kEPT2, false>(sm, logC, logNs, logNP + 1, C, 1, skew, tw, threadIdx.x);
+        if (rem == 3) fft_stage<3, kEPT2, false, SYNC>(sm, logC, logNs, logNP + 1, C, 1, skew, tw, tid);
+        else if (rem == 2) fft_stage<2, kEPT2, false, SYNC>(sm, logC, logNs, logNP + 1, C, 1, skew, tw, tid);
+        else if (rem == 1) fft_stage<1, kEPT2, false, SYNC>(sm, logC, logNs, logNP + 1, C, 1, skew, tw, tid);
     }
     float* Pt = P + (int64_t)tl * M;
     if (p.ptrans) {
@@ -816,7 +821,7 @@ __global__ void __launch_bounds__(1024, 1) k_pass2(const float2* __restrict__ Y,
         static_assert(kEPT2 % 2 == 0, "items per thread");
 #pragma unroll
         for (int r = 0; r < kEPT2 / 2; ++r) {  // items = NP C = (kEPT2 / 2) nthr
-            const int it = (int)threadIdx.x + r * nthr;
+            const int it = tid + r * nthr;
             const int ql = it & (NP - 1), k2 = it >> logNP;
             const int q = q0 + ql;
             const int lowl = ql, highl = NP + ql;
@@ -852,7 +857,7 @@ __global__ void __launch_bounds__(1024, 1) k_pass2(const float2* __restrict__ Y,
         return;
     }
     // W_N^{q + R k2} = W_N^q * W_{2C}^{k2};  W_{2C}^{k2} = tw[k2 * 8192 / (2C)]
-    const int ql = threadIdx.x & (NP - 1);
+    const int ql = tid & (NP - 1);
     const int q = q0 + ql;
     const float2 wq = twiddle((uint32_t)q, logn);
     const int twsh = 12 - logC;
@@ -860,7 +865,7 @@ __global__ void __launch_bounds__(1024, 1) k_pass2(const float2* __restrict__ Y,
     const int lo0 = lowl * skew, hi0 = highl * skew;
 #pragma unroll
     for (int r = 0; r < kEPT2 / 2; ++r) {  // items = NP C = (kEPT2 / 2) nthr
-        const int it = (int)threadIdx.x + r * nthr;
+        const int it = tid + r * nthr;
         const int k2 = it >> logNP;
         if (q != 0) {
             const int64_t k = q + ((int64_t)k2 << logR);
@@ -894,6 +899,114 @@ __global__ void __launch_bounds__(1024, 1) k_pass2(const float2* __restrict__ Y,
                 Pt[M - k] = pb;
             }
         }
+    }
+}
+
+template <int LR, int LC, int LNP>
+__global__ void __launch_bounds__(1024, 1) k_pass2(const float2* __restrict__ Y, Plan p,
+                                                  const float2* __restrict__ tw,
+                                                  float* __restrict__ P)
+{
+    extern __shared__ float2 sm[];
+    __shared__ float2 s_wq[64];
+    const int logNP = LNP >= 0 ? LNP : p.logNP;
+    pass2_tile<LR, LC, LNP, SyncCTA, false>(Y, blockIdx.y, blockIdx.x << logNP, p, tw, P, sm, s_wq,
+                                           threadIdx.x);
+}
+
+// ---- Pass 2 fed by TMA bulk copies ------------------------------------------------------
+// A persistent CTA per SM walks the pass-2 tiles (2 NP rows of C complex = 2^13 values):
+// one producer thread copies the 2 NP rows of tile i + 1 from Y into an unpadded staging
+// buffer with 1D bulk copies (each row is one contiguous run of 8 C bytes, completed on
+// the buffer's "full" mbarrier), while 16 consumer warps transform tile i: the first
+// radix-16 stage reads the staging buffer (lanes read consecutive elements: no bank
+// conflicts without padding) into the padded work tile, the rest is pass2_tile's.  The
+// buffer returns to the producer ("empty", one arrival per consumer warp) when its tile is
+// done.  Waits are bounded; on expiry the status word gets bit 2.
+constexpr int kP2Consumers = 512;
+constexpr int kP2Threads = kP2Consumers + 32;
+constexpr int kP2Stages = 2;
+constexpr int kP2Tile = 1 << 13;
+constexpr int kP2Work = kP2Tile + (kP2Tile >> 4) + 64;  // padded work tile + line skew (float2)
+
+size_t p2tma_smem()
+{
+    return 128 + (size_t)(kP2Stages * kP2Tile + kP2Work + 64) * sizeof(float2);
+}
+
+template <int LR, int LC, int LNP>
+__global__ void __launch_bounds__(kP2Threads, 1) k_pass2_tma(const float2* __restrict__ Y, Plan p,
+                                                             const float2* __restrict__ tw,
+                                                             float* __restrict__ P, int ntiles,
+                                                             unsigned long long* __restrict__ status)
+{
+    constexpr int NP = 1 << LNP;
+    constexpr int C = 1 << LC;
+    constexpr int R = 1 << LR;
+    constexpr int LTPT = LR - 1 - LNP;  // log2 of the tiles per template
+    static_assert(2 * NP * C == kP2Tile && LTPT >= 0, "tiles of 2^13 complex values");
+    extern __shared__ __align__(128) unsigned char psm[];
+    uint64_t* full = reinterpret_cast<uint64_t*>(psm);
+    uint64_t* empty = full + kP2Stages;
+    float2* stg = reinterpret_cast<float2*>(psm + 128);
+    float2* sm = stg + kP2Stages * kP2Tile;
+    float2* s_wq = sm + kP2Work;
+    if (threadIdx.x == 0) {
+#pragma unroll
+        for (int b = 0; b < kP2Stages; ++b) {
+            mbar_init(&full[b], 1);
+            mbar_init(&empty[b], kP2Consumers / 32);
+        }
+    }
+    __syncthreads();
+    const int64_t M = (int64_t)1 << (LR + LC);
+    if (threadIdx.x >= kP2Consumers) {
+        // ---- producer: lane 0 of the last warp ----
+        if (threadIdx.x != kP2Consumers) return;
+        int i = 0;
+        for (;; ++i) {
+            const int u = (int)blockIdx.x + i * (int)gridDim.x;
+            if (u >= ntiles) break;
+            const int b = i % kP2Stages, k = i / kP2Stages;
+            if (k > 0 && !mbar_wait_parity(&empty[b], (uint32_t)((k - 1) & 1))) {
+                atomicOr(status, 4ull);
+                break;
+            }
+            const int tl = u >> LTPT;
+            const int q0 = (u & ((1 << LTPT) - 1)) << LNP;
+            mbar_expect_tx(&full[b], (uint32_t)(kP2Tile * sizeof(float2)));
+#pragma unroll
+            for (int l = 0; l < 2 * NP; ++l) {
+                const int q = q0 + (l & (NP - 1));
+                const int row = (l < NP) ? q : (q == 0 ? (R >> 1) : R - q);
+                tma_load_1d(stg + b * kP2Tile + l * C, Y + (int64_t)tl * M + ((int64_t)row << LC),
+                            (uint32_t)(C * sizeof(float2)), &full[b]);
+            }
+        }
+        // let the copies issued last land before the CTA's shared memory can go away
+        for (int m = (i > kP2Stages ? i - kP2Stages : 0); m < i; ++m)
+            (void)mbar_wait_parity(&full[m % kP2Stages], (uint32_t)((m / kP2Stages) & 1));
+        return;
+    }
+    // ---- consumers ----
+    const int ct = (int)threadIdx.x;
+    for (int i = 0;; ++i) {
+        const int u = (int)blockIdx.x + i * (int)gridDim.x;
+        if (u >= ntiles) break;
+        const int b = i % kP2Stages, k = i / kP2Stages;
+        bool ok = true;
+        if (ct == 0) ok = mbar_wait_parity(&full[b], (uint32_t)(k & 1));
+        if (group_any<1>(!ok)) {
+            if (ct == 0) atomicOr(status, 4ull);
+            break;
+        }
+        const int tl = u >> LTPT;
+        const int q0 = (u & ((1 << LTPT) - 1)) << LNP;
+        pass2_tile<LR, LC, LNP, SyncNamed<1, kP2Consumers>, true>(stg + b * kP2Tile, tl, q0, p, tw, P, sm,
+                                                                  s_wq, ct);
+        SyncNamed<1, kP2Consumers>::sync();  // the work tile and s_wq are free for the next tile
+        __syncwarp();
+        if ((ct & 31) == 0) mbar_arrive(&empty[b]);
     }
 }
 
@@ -947,6 +1060,7 @@ Pass2Fn pick_pass2(const Plan& p)
 
 namespace {
 cudaError_t ws_attributes(int* nsm);
+cudaError_t p2tma_attributes(int* nsm);
 }
 
 // Large dynamic shared memory for the FFT passes, set once per device (a host-side
@@ -973,6 +1087,7 @@ cudaError_t set_smem_attributes()
 #undef BPS_ATTR
     int nsm = 0;
     if (e == cudaSuccess) e = ws_attributes(&nsm);
+    if (e == cudaSuccess) e = p2tma_attributes(&nsm);
     if (e == cudaSuccess) done[dev] = true;
     return e;
 }
@@ -1048,9 +1163,64 @@ cudaError_t launch_pass1(const SeriesView& x, const Anchor* anc, int nt, const P
     return cudaGetLastError();
 }
 
-cudaError_t launch_pass2(const float2* Y, int nt, const Plan& p, const float2* tw, float* P,
-                         cudaStream_t s)
+namespace {
+
+using P2TmaFn = void (*)(const float2*, Plan, const float2*, float*, int, unsigned long long*);
+
+// (log R, log C) of the TMA-fed pass 2 (2^13-complex tiles: NP = 2^12 / C row pairs)
+#define BPS_P2TMA_GEOMETRIES(X) \
+    X(10, 10) X(11, 10) X(12, 10) X(10, 11) X(11, 11) X(12, 11) X(10, 12) X(11, 12) X(12, 12)
+
+P2TmaFn pick_p2tma(const Plan& p)
 {
+#define BPS_PICK(a, b) \
+    if (p.logR == a && p.logC == b) return k_pass2_tma<a, b, 12 - b>;
+    BPS_P2TMA_GEOMETRIES(BPS_PICK)
+#undef BPS_PICK
+    return nullptr;
+}
+
+cudaError_t p2tma_attributes(int* nsm)
+{
+    static std::mutex mu;
+    static int done[64] = {};
+    int dev = 0;
+    cudaError_t e = cudaGetDevice(&dev);
+    if (e != cudaSuccess) return e;
+    if (dev < 0 || dev >= 64) return cudaErrorInvalidDevice;
+    std::lock_guard<std::mutex> lk(mu);
+    if (!done[dev]) {
+        const int bytes = (int)p2tma_smem();
+#define BPS_ATTR(a, b) \
+    if (e == cudaSuccess) e = cudaFuncSetAttribute(k_pass2_tma<a, b, 12 - b>, cudaFuncAttributeMaxDynamicSharedMemorySize, bytes);
+        BPS_P2TMA_GEOMETRIES(BPS_ATTR)
+#undef BPS_ATTR
+        int n = 0;
+        if (e == cudaSuccess) e = cudaDeviceGetAttribute(&n, cudaDevAttrMultiProcessorCount, dev);
+        if (e != cudaSuccess) return e;
+        done[dev] = n;
+    }
+    *nsm = done[dev];
+    return cudaSuccess;
+}
+
+}  // namespace
+
+cudaError_t launch_pass2(const float2* Y, int nt, const Plan& p, const float2* tw, float* P,
+                         unsigned long long* status, cudaStream_t s)
+{
+    if (p.p2tma) {
+        const P2TmaFn f = pick_p2tma(p);
+        if (!f || !status || p.logTile2 != 13) return cudaErrorInvalidValue;
+        int nsm = 0;
+        cudaError_t e = p2tma_attributes(&nsm);
+        if (e != cudaSuccess) return e;
+        const int64_t ntiles = (int64_t)nt << (p.logR - 1 - p.logNP);
+        if (ntiles < 1 || ntiles > INT32_MAX) return cudaErrorInvalidValue;
+        const int grid = (int)std::min<int64_t>(ntiles, nsm);
+        f<<<grid, kP2Threads, p2tma_smem(), s>>>(Y, p, tw, P, (int)ntiles, status);
+        return cudaGetLastError();
+    }
     const int logt = p.logNP + 1 + p.logC;
     cudaError_t e = set_smem_attributes();
     if (e != cudaSuccess) return e;

@@ -6,6 +6,11 @@
   for (R = 2^10, 2^11, 2^12) from 2^21 to 2^25 samples, with FP32 and FP16 series
   storage, and for batches whose tiles outnumber the CTAs (each CTA walks many tiles
   through its two buffers).
+* The TMA-fed pass 2 (one thread copies the next tile's rows into shared memory with
+  bulk copies while the consumer warps transform the current tile) gives the oracle's
+  whitened power and candidates for its splits (R, C in 2^10..2^12), alone and combined
+  with the warp-specialised pass 1, in both power layouts, and over batches whose tiles
+  outnumber the CTAs.
 * The two power layouts of pass 2 (bins in order, or row-major blocks of 8 columns that
   the whitening kernel transposes) give bit-identical whitened spectra and candidates,
   at the smallest sizes where a pass-2 CTA holds one or two row pairs.
@@ -178,3 +183,61 @@ def test_power_rows_rejected_where_not_possible(bps, ctx):
         ctx.search(sid, bid, bps.default_params(log_cols=9, power_layout=bps.BPS_POWER_ROWS))
     ctx.unload(sid)
     ctx.unload(bid)
+
+
+@pytest.mark.parametrize("logn,log_cols,p1", [(21, 10, 1), (22, 10, 1), (22, 11, 2), (23, 11, 1),
+                                              (23, 12, 2), (23, 10, 1), (24, 12, 1), (24, 11, 2)])
+def test_tma_pass2_against_oracle(bps, ctx, orc, logn, log_cols, p1):
+    x, ts, bank = _workload(logn, 4600 + logn + log_cols, K=2 if logn <= 23 else 1,
+                            ecc=(log_cols % 2 == 1))
+    n = x.size
+    sid = ctx.load_series(x, ts)
+    bid = ctx.load_bank(bank)
+    prm = bps.default_params(log_cols=log_cols, log_tile2=13, sigma_thr=5.0, pass1_kind=p1,
+                             pass2_kind=bps.BPS_PASS2_TMA)
+    pw = ctx.whitened_spectrum(sid, bid, 0, len(bank), n, prm)
+    gc, _ = ctx.fetch_candidates(ctx.search(sid, bid, prm))
+    oc, res = oracle_on_gpu_maps(ctx, orc, sid, bid, x, ts, bank, want_arrays=True, sigma=5.0)
+    for t in range(len(bank)):
+        e = pw_close(pw[t], res[t]["Pw"])
+        assert e <= PW_TOL, (t, e)
+    compare_candidates(gc, oc, bps.thresholds(prm, n, len(bank)))
+    # the one-phase pass 2 in the same launch shape gives the same candidates set (both
+    # within the power tolerance of the oracle)
+    ref, _ = ctx.fetch_candidates(ctx.search(sid, bid, bps.default_params(
+        log_cols=log_cols, log_tile2=13, sigma_thr=5.0, pass1_kind=p1, pass2_kind=bps.BPS_PASS2_FUSED)))
+    compare_candidates(gc, ref, bps.thresholds(prm, n, len(bank)), max_excused=2)
+    ctx.unload(sid)
+    ctx.unload(bid)
+
+
+def test_tma_pass2_many_tiles_and_rejects(bps, ctx, orc):
+    """24 templates of 2^21 samples (C = R = 1024: 128 tiles each) on at most one CTA per
+    SM: batched equals one template per launch and the oracle on sampled templates; the
+    TMA-fed pass 2 is refused where it is not built."""
+    logn = 21
+    n, ts = 1 << logn, 64e-6
+    T = n * ts
+    x, _, _ = _workload(logn, 4700)
+    bank, _ = synth.uniform_bank(24, 4701, (3 * T, 10 * T), (0.0, 0.3))
+    sid = ctx.load_series(x, ts)
+    bid = ctx.load_bank(bank)
+    res = {}
+    for batch in (24, 1, 5):
+        prm = bps.default_params(log_cols=10, log_tile2=13, batch=batch, sigma_thr=4.5,
+                                 pass2_kind=bps.BPS_PASS2_TMA)
+        res[batch] = ctx.fetch_candidates(ctx.search(sid, bid, prm))[0]
+    assert np.array_equal(res[24], res[1]) and np.array_equal(res[5], res[1])
+    sample = [3, 17]
+    sbid = ctx.load_bank(bank[sample])
+    oc, _ = oracle_on_gpu_maps(ctx, orc, sid, sbid, x, ts, bank[sample], sigma=4.5)
+    oc["template_idx"] = np.array(sample)[oc["template_idx"]]
+    compare_candidates(res[24][np.isin(res[24]["template_idx"], sample)], oc,
+                       bps.thresholds(prm, n, 24))
+    with pytest.raises(bps.BpsError):  # 2^14 pass-2 tiles
+        ctx.search(sid, bid, bps.default_params(log_cols=10, log_tile2=14,
+                                                pass2_kind=bps.BPS_PASS2_TMA))
+    with pytest.raises(bps.BpsError):  # C = 2^9
+        ctx.search(sid, bid, bps.default_params(log_cols=9, pass2_kind=bps.BPS_PASS2_TMA))
+    for i in (sid, bid, sbid):
+        ctx.unload(i)

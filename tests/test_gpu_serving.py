@@ -137,8 +137,6 @@ def test_resident_series_same_results(bps, ctx):
         assert not srv.series_info(ids[0])["resident"]
         tickets = [srv.submit_series(i, bank, prm) for i, (_, _, bank, _) in zip(ids, reqs)]
         tickets += [srv.submit_series(i, bank, prm) for i, (_, _, bank, _) in zip(ids, reqs)][::-1]
-        with pytest.raises(bps.BpsError):
-            srv.unload_series(ids[0])  # named by unfinished requests
         res = [srv.result(t)[0] for t in tickets]
         for i in range(len(reqs)):
             assert np.array_equal(res[i], ref[i]), i
@@ -180,3 +178,22 @@ def test_resident_series_lru_eviction(bps, ctx):
         ref = [big.result(big.submit(x, ts, bank, prm))[0] for x in xs]
     for j, c in zip(order, out):
         assert np.array_equal(c, ref[j]), j
+
+
+def test_resident_series_pinned_while_named(bps, ctx):
+    """A series named by an unfinished request cannot be unloaded; once its requests are
+    done it can, and then it can no longer be named."""
+    n, ts = 1 << 22, 64e-6
+    T = n * ts
+    x = synth.noise(n, 650)
+    bank, _ = synth.uniform_bank(2048, 651, (3 * T, 10 * T), (0.0, 1.0))  # ~50 ms of work
+    prm = bps.default_params(cand_cap=1 << 12)
+    with bps.Server(ctx, max_active=1) as srv:
+        sid = srv.load_series(x, ts)
+        t = srv.submit_series(sid, bank, prm)
+        with pytest.raises(bps.BpsError):
+            srv.unload_series(sid)
+        srv.result(t, allow_overflow=True)
+        srv.unload_series(sid)
+        with pytest.raises(bps.BpsError):
+            srv.submit_series(sid, bank, prm)
