@@ -200,11 +200,12 @@ def plain_circular(n: int = 1 << 20, K: int = 32, seed: int = 1, with_series=Tru
 
 
 def htru_circular(n: int = 1 << 23, K: int = 4096, seed: int = 2, with_series=True,
-                  amp: float = 0.3) -> Workload:
+                  amp: float = 0.02) -> Workload:
     """HTRU-like: 2^23 samples at 64 us (537 s), N(0,1) + 3 pulsar-BH binaries
     (P U[20,100] ms, m_p 1.4, m_c 10 Msun, Porb U[3T,10T], cos i U[0,1),
-    tau = tau_max sin i, peak amplitude 0.3 sigma as in the 2^20 workload);
-    K-3 templates Porb U[3T,10T], tau U[0,3] lt-s, phi U."""
+    tau = tau_max sin i, peak amplitude 0.02 sigma: the single-pulse S/N of the
+    paper's simulations, Table 2); K-3 templates Porb U[3T,10T], tau U[0,3] lt-s,
+    phi U."""
     tsamp = 64e-6
     T = n * tsamp
     rng = np.random.default_rng(seed + 200)
@@ -227,7 +228,7 @@ def htru_circular(n: int = 1 << 23, K: int = 4096, seed: int = 2, with_series=Tr
     return w
 
 
-def pulsar_bh_series(n: int, tsamp: float, seed: int, amp: float = 0.3):
+def pulsar_bh_series(n: int, tsamp: float, seed: int, amp: float = 0.02):
     """N(0,1) series with one pulsar-BH binary drawn as in htru_circular (P U[20,100] ms,
     m_c 10 Msun, Porb U[3T,10T], tau = tau_max sin i).  Returns (series, Pulsar)."""
     T = n * tsamp
@@ -243,9 +244,9 @@ def pulsar_bh_series(n: int, tsamp: float, seed: int, amp: float = 0.3):
 
 
 def elliptical_imbh(n: int = 1 << 25, K: int = 2048, seed: int = 3, with_series=True,
-                    amp: float = 0.3) -> Workload:
+                    amp: float = 0.02) -> Workload:
     """Elliptical IMBH-in-globular-cluster: 2^25 samples at 128 us, 2 pulsars with
-    e = 0.05 and 0.09 (P U[20,40] ms, peak amplitude 0.3 sigma as in the other workloads);
+    e = 0.05 and 0.09 (P U[20,40] ms, peak amplitude 0.02 sigma as in Table 2);
     K-2 templates Porb U[5T,10T], tau U[0,20], phi, omega U[0,2pi), e U[0,0.1]."""
     tsamp = 128e-6
     T = n * tsamp
