@@ -284,7 +284,8 @@ def run_reference(args, ws, rank):
 def serving_pool(seed=5):
     """Seeded series for the serving sweep: three per length 2^20..2^24 at 64 us, the
     first with one injected pulsar-BH binary (0-1 pulsar per request)."""
-    return {logn: [synth.pulsar_bh_series(1 << logn, 64e-6, 3000 + 10 * logn)[0]] +
+    return {logn: [synth.pulsar_bh_series(1 << logn, 64e-6, 3000 + 10 * logn,
+                                          amp=synth.equal_snr_amp(1 << logn))[0]] +
             [synth.noise(1 << logn, 3000 + 10 * logn + i) for i in (1, 2)]
             for logn in range(20, 25)}
 
@@ -357,7 +358,8 @@ SERVING_WORKLOAD = ("Poisson arrivals; series 2^20-2^24 (log-uniform) x 64 us, F
 
 def run_uneven(bps, ctx, steps=2, warmup=1, seed=11):
     """Batched uneven search: 64 series of random length 2^21..2^24 at 64 us, each with
-    one injected pulsar-BH binary (as in the 2^23 workload) and its own bank of
+    one injected pulsar-BH binary (as in the 2^23 workload, peak amplitude scaled as
+    0.02 sqrt(2^23 / n) for the same per-harmonic signal-to-noise) and its own bank of
     256..2048 circular templates (Porb U[3T,10T], tau U[0,3] lt-s, phi U) that includes
     the true orbit; launch shapes autotuned per length, all 64 searches captured in one
     CUDA graph and replayed; device time per replay by CUDA events on the launching
@@ -372,7 +374,7 @@ def run_uneven(bps, ctx, steps=2, warmup=1, seed=11):
         n, ts = 1 << logn, 64e-6
         T = n * ts
         k = int(rng.integers(256, 2049))
-        x, p = synth.pulsar_bh_series(n, ts, 6000 + i)
+        x, p = synth.pulsar_bh_series(n, ts, 6000 + i, amp=synth.equal_snr_amp(n))
         bank, where = synth.uniform_bank(k, 5000 + i, (3 * T, 10 * T), (0.0, 3.0),
                                          true_orbits=[p.orbit()])
         sid = ctx.load_series(x, ts)
@@ -409,7 +411,8 @@ def run_uneven(bps, ctx, steps=2, warmup=1, seed=11):
     for x in ids:
         ctx.unload(x)
     return {"workload": "64 series of 2^21-2^24 samples (random) x 64 us, one injected pulsar-BH "
-                        "binary each, each with 256-2048 circular templates (Porb U[3T,10T], "
+                        "binary each (peak amplitude 0.02 sqrt(2^23/n)), each with 256-2048 "
+                        "circular templates (Porb U[3T,10T], "
                         "tau U[0,3] lt-s) including its true orbit; one CUDA graph over the 64 "
                         "searches (4 parallel branches), launch shapes autotuned per length",
             "templates": K, "value": K / (statistics.mean(ms) / 1e3), "unit": UNIT,

@@ -228,6 +228,12 @@ def htru_circular(n: int = 1 << 23, K: int = 4096, seed: int = 2, with_series=Tr
     return w
 
 
+def equal_snr_amp(n: int, amp_2p23: float = 0.02) -> float:
+    """Peak amplitude that gives a pulse train in n samples the per-harmonic signal-to-noise
+    of amplitude amp_2p23 in 2^23 samples (the coherent power grows as amp^2 n)."""
+    return amp_2p23 * math.sqrt((1 << 23) / n)
+
+
 def pulsar_bh_series(n: int, tsamp: float, seed: int, amp: float = 0.02):
     """N(0,1) series with one pulsar-BH binary drawn as in htru_circular (P U[20,100] ms,
     m_c 10 Msun, Porb U[3T,10T], tau = tau_max sin i).  Returns (series, Pulsar)."""
