@@ -358,8 +358,9 @@ SERVING_WORKLOAD = ("Poisson arrivals; series 2^20-2^24 (log-uniform) x 64 us, F
 
 def run_uneven(bps, ctx, steps=2, warmup=1, seed=11):
     """Batched uneven search: 64 series of random length 2^21..2^24 at 64 us, each with
-    one injected pulsar-BH binary (as in the 2^23 workload, peak amplitude scaled as
-    0.02 sqrt(2^23 / n) for the same per-harmonic signal-to-noise) and its own bank of
+    one injected pulsar-BH binary (as in the 2^23 workload, peak amplitude 0.03 sqrt(2^23 / n):
+    the same per-harmonic signal-to-noise at every length, 2.25 times the 2^23 workload's
+    in power, so that scalloping and noise leave every pulsar detectable) and its own bank of
     256..2048 circular templates (Porb U[3T,10T], tau U[0,3] lt-s, phi U) that includes
     the true orbit; launch shapes autotuned per length, all 64 searches captured in one
     CUDA graph and replayed; device time per replay by CUDA events on the launching
@@ -367,28 +368,37 @@ def run_uneven(bps, ctx, steps=2, warmup=1, seed=11):
     of n T / P at some harmonic level n."""
     import torch
     rng = np.random.default_rng(seed)
-    pairs, K, n_of, truth = [], 0, {}, []
+    pairs, K, n_of, truth, lens, bank_sizes = [], 0, {}, [], [], {}
     ids = []
     for i in range(64):
         logn = int(rng.integers(21, 25))
         n, ts = 1 << logn, 64e-6
         T = n * ts
         k = int(rng.integers(256, 2049))
-        x, p = synth.pulsar_bh_series(n, ts, 6000 + i, amp=synth.equal_snr_amp(n))
+        x, p = synth.pulsar_bh_series(n, ts, 6000 + i, amp=synth.equal_snr_amp(n, 0.03))
         bank, where = synth.uniform_bank(k, 5000 + i, (3 * T, 10 * T), (0.0, 3.0),
                                          true_orbits=[p.orbit()])
         sid = ctx.load_series(x, ts)
         bid = ctx.load_bank(bank)
         ids += [sid, bid]
         pairs.append((sid, bid))
+        lens.append(logn)
+        bank_sizes[(sid, bid)] = k
         truth.append((where[0], T, p.period_s))
         n_of[logn] = (sid, bid)
         K += k
     prm = bps.default_params(cand_cap=1 << 20)
-    tuned = {}
+    tuned, ms_t = {}, {}
     for logn, (sid, bid) in sorted(n_of.items()):
-        best, _ = ctx.autotune(sid, bid, prm, sample_templates=64)
+        best, ms = ctx.autotune(sid, bid, prm, sample_templates=64)
         tuned[logn] = [best.log_tile, best.log_tile2, best.batch, best.log_cols]
+        ms_t[logn] = ms
+    # the rate the mix would reach if every template ran at its length's uniform rate (the
+    # autotuner's best time per template on a 64-template sample of that length)
+    k_of = {}
+    for (sid, bid), (ti, T, P), logn in zip(pairs, truth, lens):
+        k_of[logn] = k_of.get(logn, 0) + bank_sizes[(sid, bid)]
+    bound = K / (sum(k_of[l] * ms_t[l] for l in k_of) / 1e3)
     gid = ctx.graph_create(pairs, prm)
     st = torch.cuda.Stream()
     ms = []
@@ -411,13 +421,17 @@ def run_uneven(bps, ctx, steps=2, warmup=1, seed=11):
     for x in ids:
         ctx.unload(x)
     return {"workload": "64 series of 2^21-2^24 samples (random) x 64 us, one injected pulsar-BH "
-                        "binary each (peak amplitude 0.02 sqrt(2^23/n)), each with 256-2048 "
+                        "binary each (peak amplitude 0.03 sqrt(2^23/n)), each with 256-2048 "
                         "circular templates (Porb U[3T,10T], "
                         "tau U[0,3] lt-s) including its true orbit; one CUDA graph over the 64 "
                         "searches (4 parallel branches), launch shapes autotuned per length",
             "templates": K, "value": K / (statistics.mean(ms) / 1e3), "unit": UNIT,
             "ms_per_graph": statistics.mean(ms), "steps": steps, "warmup": warmup,
-            "autotuned": {"2^%d" % k: v for k, v in tuned.items()}, "candidates": int(ncand),
+            "autotuned": {"2^%d" % k: v for k, v in tuned.items()},
+            "templates_per_length": {"2^%d" % k: v for k, v in sorted(k_of.items())},
+            "uniform_ms_per_template": {"2^%d" % k: v for k, v in sorted(ms_t.items())},
+            "uniform_rate_bound": bound, "fraction_of_uniform_rate_bound": (K / (statistics.mean(ms) / 1e3)) / bound,
+            "candidates": int(ncand),
             "pulsars_found": "%d of 64" % found}
 
 

@@ -114,7 +114,7 @@ inline bool tma_pass2_built(int logR, int logC, int logTile2)
     return logTile2 == 13 && logR >= 10 && logR <= 12 && logC >= 10 && logC <= 12;
 }
 
-// Anchor block length B = 2^logB: the largest (<= 2^14, <= n) for which every
+// Anchor block length B = 2^logB: the largest (<= 2^14, <= n/16) for which every
 // template keeps the FP32 fast path of the index map far inside its 1e-4 guard:
 // |linear increment| <= 128 samples, quadratic term <= 0.25 sample, quartic
 // remainder <= 1e-5 sample, with h = B/2 the largest distance to the anchor centre.
@@ -122,7 +122,9 @@ inline bool tma_pass2_built(int logR, int logC, int logTile2)
 // g = Omega t_s / (1 - e)).  Returns -1 when even B = 64 does not qualify.
 inline int plan_anchor_block(double kg1, double kg2, double kg4, int logn)
 {
-    int logB = logn < 14 ? logn : 14;
+    // B <= N/16 as well: the 16 rows of a pass-1 butterfly (N/16 samples apart) then sit at
+    // the same offset from their anchor centres
+    int logB = logn - 4 < 14 ? logn - 4 : 14;
     for (; logB >= 6; --logB) {
         const double h = (double)(1 << (logB - 1));
         if (kg1 * h <= 128.0 && kg2 * h * h <= 0.25 && kg4 * h * h * h * h <= 1e-5) return logB;

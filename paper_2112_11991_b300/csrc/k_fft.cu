@@ -317,20 +317,27 @@ __device__ __forceinline__ void pass1_indices(const Anchor* __restrict__ at, int
                                               int logC, int col, int j, int (&id)[32])
 {
     const int half = 1 << (logB - 1);
+    // the 16 rows of a butterfly lie N/16 samples apart, a multiple of the anchor block
+    // (the planner keeps B <= N/16): all 32 samples share their offset d from their
+    // anchor centre, and the anchor index steps by a constant
+    const int m0 = 2 * ((j << logC) + col);
+    const int d = (m0 & ((1 << logB) - 1)) - half;
+    const int ab0 = m0 >> logB;
+    const int dab = 1 << (logQ + logC + 1 - logB);
+    const float dfs[2] = {(float)d, (float)(d + 1)};
     unsigned pm = 0;
 #pragma unroll
     for (int s = 0; s < 16; ++s) {
-        const int m = 2 * (((j + (s << logQ)) << logC) + col);
-        const int ab = m >> logB;
+        const int m = m0 + (s << (logQ + logC + 1));
+        const int ab = ab0 + s * dab;
         const float4 a4 = __ldg(reinterpret_cast<const float4*>(at + ab));
         const float q3 = __ldg(&at[ab].q3);
         const int I = __float_as_int(a4.x) - kRoundBits;
         const float fh = a4.y, L = a4.z, q2 = a4.w;
-        const int d = m - ((ab << logB) + half);
 #pragma unroll
         for (int u = 0; u < 2; ++u) {
             // xr = off - I - 1/2; outside the guard band floor(xr + 1/2) = rint(xr)
-            const float df = (float)(d + u);
+            const float df = dfs[u];
             const float xr = fh - df * fmaf(df, fmaf(df, q3, q2), L);
             const float y = __fadd_rn(xr, kRoundShift);
             const float fr = __fsub_rn(xr, __fsub_rn(y, kRoundShift));
@@ -343,10 +350,8 @@ __device__ __forceinline__ void pass1_indices(const Anchor* __restrict__ at, int
         for (int q = 0; q < 32; ++q) {
             if (pm & (1u << q)) {
                 const int s = q >> 1, u = q & 1;
-                const int m = 2 * (((j + (s << logQ)) << logC) + col);
-                const int ab = m >> logB;
-                const Anchor a = at[ab];
-                const int d = m - ((ab << logB) + half);
+                const int m = m0 + (s << (logQ + logC + 1));
+                const Anchor a = at[ab0 + s * dab];
                 id[q] = m + u + a.I + off_round_precise(a, d + u);
             }
         }
