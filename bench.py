@@ -104,12 +104,18 @@ def kernel_source_hash():
     return h.hexdigest()[:16]
 
 
-def geometry_key(logn, log_cols, log_tile, log_tile2):
+def geometry_key(logn, log_cols, log_tile, log_tile2, pass1_kind=0, pass2_kind=0):
     """Traffic key of a launch shape: four-step split and the two pass tiles (0 = the
-    library's defaults: C = 2^min(10, log M - 5) raised to M / 2^12, tiles 14 / 13)."""
+    library's defaults: C = 2^min(10, log M - 5) raised to M / 2^12, tiles 14 / 13), with
+    a suffix for the warp-specialised pass 1 and the TMA-fed pass 2."""
     logM = logn - 1
     lc = log_cols or (min(10, logM - 5) if logM - min(10, logM - 5) <= 12 else logM - 12)
-    return "c%d_t%d_%d" % (lc, log_tile or 14, log_tile2 or 13)
+    key = "c%d_t%d_%d" % (lc, log_tile or 14, log_tile2 or 13)
+    if pass1_kind == 2:
+        key += "_p1ws"
+    if pass2_kind == 2:
+        key += "_p2tma"
+    return key
 
 
 def ncu_traffic(stage, workload, templates_per_launch, geom):
@@ -637,9 +643,11 @@ def main():
     alg_bytes = STAGE_BYTES_PER_N[dom] * n * batch
     achieved = alg_bytes / (per_launch_ms * 1e-3) / 1e9
     if tuned:
-        geom = geometry_key(args.logn, tuned["log_cols"], tuned["log_tile"], tuned["log_tile2"])
+        geom = geometry_key(args.logn, tuned["log_cols"], tuned["log_tile"], tuned["log_tile2"],
+                            tuned["pass1_kind"], tuned["pass2_kind"])
     else:
-        geom = geometry_key(args.logn, args.log_cols, args.log_tile, args.log_tile2)
+        geom = geometry_key(args.logn, args.log_cols, args.log_tile, args.log_tile2,
+                            args.pass1_kind, args.pass2_kind)
     traffic = ncu_traffic(dom, "htru_2p%d" % args.logn, batch, geom)
     roof = {"bound": "hbm", "kernel": dom, "achieved": achieved, "peak": peak, "unit": "GB/s",
             "frac": achieved / peak, "peak_kind": peak_kind, "traffic": traffic,
