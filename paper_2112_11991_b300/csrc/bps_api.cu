@@ -374,7 +374,7 @@ try {
     if (out && nw > 0) std::memcpy(out, r.result.data(), sizeof(bps_candidate) * nw);
     if (n_written) *n_written = out ? nw : 0;
     if (n_total) *n_total = (int64_t)r.total;
-    if (r.status & 1ull)
+    if (r.status != 0)
         return fail(ctx, BPS_ERR_TIMEOUT, "request %lld: a bounded device wait expired; "
                     "results incomplete", (long long)req_id);
     if ((int64_t)r.total > r.cap)
@@ -636,7 +636,7 @@ try {
     if (out && nw > 0) std::memcpy(out, r.data(), sizeof(bps_candidate) * nw);
     if (n_written) *n_written = out ? nw : 0;
     if (n_total) *n_total = (int64_t)g.totals[pair];
-    if (g.status[pair] & 1ull) return fail(ctx, BPS_ERR_TIMEOUT, "a bounded device wait expired");
+    if (g.status[pair] != 0) return fail(ctx, BPS_ERR_TIMEOUT, "a bounded device wait expired");
     if ((int64_t)g.totals[pair] > g.cap)
         return fail(ctx, BPS_ERR_CAND_OVERFLOW, "pair %lld: %llu candidates, capacity %lld",
                     (long long)pair, g.totals[pair], (long long)g.cap);

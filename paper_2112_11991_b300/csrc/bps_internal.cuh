@@ -194,7 +194,8 @@ cudaError_t launch_block_median(float* P, int nt, const Plan& p, float* scale,
 cudaError_t launch_whitened(const float* P, const float* scale, int nt, const Plan& p,
                             float* out, cudaStream_t s);
 // P holds the whitened spectrum (after launch_block_median); scale unused.  count[0]
-// is the candidate counter, count[1] a status word (bit 0: a bounded wait expired).
+// is the candidate counter, count[1] a status word (bit 0: a bounded wait of the harmonic sum
+// expired; bits 1 and 2 are set by the producer/consumer forms of passes 1 and 2).
 cudaError_t launch_harmsum(const float* P, const float* scale, int nt, int64_t tidx0,
                            const Plan& p, const Thr& thr, Cand* cands, int64_t cap,
                            unsigned long long* count, float* s_out, cudaStream_t s);

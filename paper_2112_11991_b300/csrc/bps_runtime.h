@@ -55,7 +55,8 @@ struct Request {
     int64_t cap = 0;
     bool synced = false;
     unsigned long long total = 0;
-    unsigned long long status = 0;  // bit 0: a bounded device wait expired
+    unsigned long long status = 0;  // non-zero: a bounded device wait expired (bit 0 harmonic
+                                    // sum, bit 1 warp-specialised pass 1, bit 2 TMA-fed pass 2)
     std::vector<bps_candidate> result;
 };
 

@@ -44,6 +44,7 @@ struct SReq {
     int64_t ticket = 0;
     SState state = S_QUEUED;
     SSeries* ser = nullptr;     // resident series the request names (nullptr: its own copy)
+    bool staged_here = false;   // this request's admission began staging ser
     float* h_series = nullptr;  // pinned host copy of the submitted series
     int64_t n = 0;
     double tsamp = 0;
@@ -304,7 +305,10 @@ bool admit_one(bps_server* srv, SReq& q, int slot)
     if (q.ser) {
         SSeries& ser = *q.ser;
         ser.last_use = now_s();
-        if (!ser.resident && !ser.staging) chk(stage_series(srv, ser, st));
+        if (!ser.resident && !ser.staging) {
+            q.staged_here = true;
+            chk(stage_series(srv, ser, st));
+        }
         if (ok) chk(cudaStreamWaitEvent(st, ser.ready, 0));
         chk(pool_alloc(srv->ctx, (void**)&q.b.d, sizeof(DevTemplate) * q.bank.size(), st));
         chk(pool_alloc(srv->ctx, (void**)&q.d_cands, sizeof(Cand) * (size_t)q.prm.cand_cap, st));
@@ -358,6 +362,9 @@ void finish(bps_server* srv, SReq& q, SState st_)
     srv->busy[q.slot] = 0;
     srv->used -= q.bytes;
     if (q.ser) {
+        // a failed request that began staging its series takes the half-staged copy down
+        // (its stream is synchronised; requests waiting on the series then fail too)
+        if (st_ == S_FAILED && q.staged_here && q.ser->staging) evict_series(srv, *q.ser);
         q.ser->refs -= 1;
         q.ser->last_use = now_s();
     }
@@ -374,6 +381,13 @@ bool advance(bps_server* srv, SReq& q)
             if (cudaEventQuery(q.ev) != cudaSuccess) return false;
             if (q.ser) {
                 SSeries& ser = *q.ser;
+                if (!ser.staging && !ser.resident) {  // its staging failed and was taken down
+                    q.rc = BPS_ERR_CUDA;
+                    q.err = "staging the resident series failed";
+                    cudaStreamSynchronize(st);
+                    finish(srv, q, S_FAILED);
+                    return true;
+                }
                 if (ser.staging) {  // the series' staging has completed (the event waited on it)
                     if (ser.d_stage) {
                         cudaFreeAsync(ser.d_stage, st);
@@ -463,7 +477,7 @@ bool advance(bps_server* srv, SReq& q)
             if (kept > 0 && kept <= kPinnedCands)
                 std::memcpy(q.result.data(), q.h_cands, sizeof(Cand) * kept);
             sort_candidates(q.result);
-            if (q.status & 1ull) {
+            if (q.status != 0) {
                 q.rc = BPS_ERR_TIMEOUT;
                 q.err = "a bounded device wait expired; results incomplete";
             } else if ((int64_t)q.total > q.prm.cand_cap) {

@@ -42,6 +42,15 @@ __device__ __forceinline__ float2 cmul(float2 a, float2 b)
 }
 
 __device__ __forceinline__ float2 cadd(float2 a, float2 b) { return make_float2(a.x + b.x, a.y + b.y); }
+
+// Read-only load that does not allocate in L1 (data read once: the twiddle tables keep
+// the L1 to themselves)
+__device__ __forceinline__ float2 ld_once(const float2* p)
+{
+    float2 v;
+    asm("ld.global.nc.L1::no_allocate.v2.f32 {%0, %1}, [%2];" : "=f"(v.x), "=f"(v.y) : "l"(p));
+    return v;
+}
 __device__ __forceinline__ float2 csub(float2 a, float2 b) { return make_float2(a.x - b.x, a.y - b.y); }
 __device__ __forceinline__ float2 mul_negi(float2 a) { return make_float2(a.y, -a.x); }  // a * (-i)
 
@@ -791,7 +800,7 @@ __device__ __forceinline__ void pass2_tile(const float2* __restrict__ src, int t
         } else {
             const float2* rs = Yt + ((int64_t)row << logC) + j;
 #pragma unroll
-            for (int s = 0; s < 16; ++s) v[s] = __ldg(rs + (s << logQ));
+            for (int s = 0; s < 16; ++s) v[s] = ld_once(rs + (s << logQ));
         }
         Radix<4>::dft(v);
         const int base = line * C + 16 * j;
