@@ -120,6 +120,9 @@ typedef struct {
 #define BPS_PASS1_WARPSPEC  2  /* warp-specialised: producer warps gather tile i+1 while     */
                                /* consumer warps FFT tile i (2^13-complex tiles; built for   */
                                /* R = 2^10..2^12 and 2^21..2^25 samples, else INVALID_ARG)   */
+#define BPS_PASS1_ASYNC     3  /* one phase per tile with the gather as asynchronous copies  */
+                               /* into shared memory: 2^13 tiles, two CTAs per SM (same     */
+                               /* splits as WARPSPEC; FP16 series use the one-phase kernel)  */
 
 /* bps_search_params.power_layout (results are identical; only the memory traffic differs) */
 #define BPS_POWER_AUTO      0  /* row-major when a pass-2 CTA holds at most two row pairs,   */

@@ -35,6 +35,7 @@ BPS_MODE_PLAIN = 1
 BPS_PASS1_AUTO = 0
 BPS_PASS1_FUSED = 1
 BPS_PASS1_WARPSPEC = 2
+BPS_PASS1_ASYNC = 3
 BPS_POWER_AUTO = 0
 BPS_POWER_BINS = 1
 BPS_POWER_ROWS = 2

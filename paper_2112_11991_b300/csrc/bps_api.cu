@@ -682,9 +682,12 @@ try {
     bps_search_params bp = *base;
     // pass 1: the one-phase kernel at both tiles, and the warp-specialised one where built
     std::vector<std::pair<int, int>> p1;  // (kind, tile)
-    if (base->pass1_kind != BPS_PASS1_WARPSPEC)
+    if (base->pass1_kind == BPS_PASS1_AUTO || base->pass1_kind == BPS_PASS1_FUSED)
         for (int t : tiles) p1.push_back({BPS_PASS1_FUSED, t});
-    if (base->mode == BPS_MODE_FUSED && base->pass1_kind != BPS_PASS1_FUSED) p1.push_back({BPS_PASS1_WARPSPEC, 13});
+    if (base->mode == BPS_MODE_FUSED && (base->pass1_kind == BPS_PASS1_AUTO || base->pass1_kind == BPS_PASS1_WARPSPEC))
+        p1.push_back({BPS_PASS1_WARPSPEC, 13});
+    if (base->mode == BPS_MODE_FUSED && (base->pass1_kind == BPS_PASS1_AUTO || base->pass1_kind == BPS_PASS1_ASYNC))
+        p1.push_back({BPS_PASS1_ASYNC, 13});
     // pass 2: the one-phase kernel at both tiles, and the TMA-fed one (2^13 tiles) where built
     std::vector<std::pair<int, int>> p2;  // (kind, tile)
     if (base->pass2_kind != BPS_PASS2_TMA)
@@ -696,7 +699,7 @@ try {
             for (int nb : batches) {
                 if (nb > sub.K) continue;
                 const int lcx = lc ? lc : default_log_cols(logM);
-                if (k1.first == BPS_PASS1_WARPSPEC && !ws_pass1_built(logM - lcx, lcx)) continue;
+                if (k1.first != BPS_PASS1_FUSED && !ws_pass1_built(logM - lcx, lcx)) continue;
                 if (k2.first == BPS_PASS2_TMA && !tma_pass2_built(logM - lcx, lcx, 13)) continue;
                 bps_search_params pr = *base;
                 pr.pass1_kind = k1.first;

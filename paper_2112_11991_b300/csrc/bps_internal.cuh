@@ -60,6 +60,8 @@ struct Plan {
     int ptrans;     // 1: pass 2 writes the power row-major by k1, P'[k1 C + k2] for bin
                     // k1 + R k2, and the median kernel transposes it into bin order
     int p1ws;       // 1: warp-specialised pass 1 (producer warps gather, consumer warps FFT)
+    int p1async;    // 1: pass 1 with cp.async gathers, 2^13 tiles, two CTAs per SM (FP32
+                    // series with a device fill value; the one-phase kernel otherwise)
     int p2tma;      // 1: pass 2 fed by TMA bulk copies of its rows (persistent, 2^13 tiles)
     double tsamp;
 };
@@ -105,6 +107,7 @@ inline void plan_geometry(Plan& p, int logTile = 14, int logTile2 = 13, int logC
     if (p.logNP < 0) p.logNP = 0;
     p.ptrans = 0;
     p.p1ws = 0;
+    p.p1async = 0;
     p.p2tma = 0;
 }
 

@@ -185,7 +185,7 @@ inline int check_params(bps_ctx* ctx, const bps_search_params* pr, int64_t n)
     if (pr->log_cols != 0 && !log_cols_ok(ilog2(n) - 1, pr->log_cols))
         return fail(ctx, BPS_ERR_INVALID_ARG, "log_cols %d is not a valid split of %lld samples",
                     pr->log_cols, (long long)n);
-    if (pr->pass1_kind < BPS_PASS1_AUTO || pr->pass1_kind > BPS_PASS1_WARPSPEC)
+    if (pr->pass1_kind < BPS_PASS1_AUTO || pr->pass1_kind > BPS_PASS1_ASYNC)
         return fail(ctx, BPS_ERR_INVALID_ARG, "unknown pass1_kind %d", pr->pass1_kind);
     if (pr->power_layout < BPS_POWER_AUTO || pr->power_layout > BPS_POWER_ROWS)
         return fail(ctx, BPS_ERR_INVALID_ARG, "unknown power_layout %d", pr->power_layout);
@@ -240,14 +240,15 @@ inline int make_plan(bps_ctx* ctx, const Series& s, const Bank& b, const bps_sea
     int kind = pr.pass1_kind;
     if (kind == BPS_PASS1_AUTO)
         kind = (tuned && !pr.log_cols && !pr.log_tile) ? p1k : BPS_PASS1_FUSED;
-    if (pr.mode == BPS_MODE_FUSED && kind == BPS_PASS1_WARPSPEC) {
+    if (pr.mode == BPS_MODE_FUSED && (kind == BPS_PASS1_WARPSPEC || kind == BPS_PASS1_ASYNC)) {
         if (!ws_pass1_built(p.logR, p.logC)) {
-            if (pr.pass1_kind == BPS_PASS1_WARPSPEC)
+            if (pr.pass1_kind == kind)
                 return fail(ctx, BPS_ERR_INVALID_ARG,
-                            "the warp-specialised pass 1 is not built for R = 2^%d, C = 2^%d",
-                            p.logR, p.logC);
-        } else {
+                            "this pass-1 form is not built for R = 2^%d, C = 2^%d", p.logR, p.logC);
+        } else if (kind == BPS_PASS1_WARPSPEC) {
             p.p1ws = 1;
+        } else {
+            p.p1async = 1;
         }
     }
     // pass-2 organisation, chosen like pass 1's

@@ -525,7 +525,7 @@ __device__ __forceinline__ void ws_last_stage(const float2* __restrict__ sm, int
 
 // A middle radix-16 Stockham stage of the consumers (Ns = 2^logNs > 1, one butterfly per
 // thread), stage twiddles from the CTA's table stw: stw[k] = W_{16 Ns}^k, k < Ns.
-template <int LG>
+template <int LG, class SYNC = SyncNamed<1, kWsConsumers>>
 __device__ __forceinline__ void ws_mid_stage(float2* buf, int logR, int logNs, const float2* stw, int tid)
 {
     constexpr int G = 1 << LG;
@@ -549,11 +549,11 @@ __device__ __forceinline__ void ws_mid_stage(float2* buf, int logR, int logNs, c
         for (int s = 1; s < 16; ++s) v[s] = cmul(v[s], w[s]);
     }
     const int dst = line + G * (((j >> logNs) << (logNs + 4)) + k);
-    SyncNamed<1, kWsConsumers>::sync();
+    SYNC::sync();
     Radix<4>::dft(v);
 #pragma unroll
     for (int s = 0; s < 16; ++s) buf[pad(dst + G * s * Ns)] = v[Radix<4>::out_pos(s)];
-    SyncNamed<1, kWsConsumers>::sync();
+    SYNC::sync();
 }
 
 // Index map (FP32 fast path, compensated branch inside the guard band) and gather of the
@@ -928,6 +928,76 @@ __global__ void __launch_bounds__(1024, 1) k_pass2(const float2* __restrict__ Y,
                                            threadIdx.x);
 }
 
+// ---- Pass 1 with asynchronous gathers, two CTAs per SM ----------------------------------
+// The one-phase organisation of k_pass1 (each thread gathers the 32 samples of its first
+// radix-16 butterfly, then all run the column FFTs of the tile), with the gather issued as
+// 4-byte cp.async copies straight into the tile: no register holds a sample while the L2
+// answers, so 16 elements per thread fit 64 registers and two 512-thread CTAs (2^13 tiles)
+// share an SM, one gathering while the other transforms.  Index map as k_pass1's (one
+// anchor offset per butterfly); FP32 series with a device copy of the fill value only.
+template <int LR, int LC>
+__global__ void __launch_bounds__(512, 2) k_pass1_async(SeriesView x, const Anchor* __restrict__ anc,
+                                                        Plan p, const float2* __restrict__ tw,
+                                                        float2* __restrict__ Y)
+{
+    constexpr int LG = 13 - LR;
+    constexpr int G = 1 << LG;
+    constexpr int LM = LR + LC;
+    constexpr int LQ = LR - 4;
+    constexpr int LNS_LAST = ((LR - 1) / 4) * 4;
+    constexpr int RL_LAST = LR - LNS_LAST;
+    static_assert(LNS_LAST == 8, "stages 16 x 16 x (R / 256)");
+    extern __shared__ __align__(16) float2 asm_[];
+    float2* sm = asm_;
+    float2* stw = asm_ + kWsBufStride;  // [0, 16): W_256^k; [16, 272): last stage
+    const int tid = (int)threadIdx.x;
+    const int tl = blockIdx.y;
+    const int c0 = blockIdx.x << LG;
+    const int n = 2 << LM;
+    resolve_fill(x);
+    if (tid < 16) stw[tid] = __ldg(tw + (tid << (13 - 8)));
+    if (tid < 256) stw[16 + tid] = __ldg(tw + (tid << (13 - LNS_LAST - RL_LAST)));
+    // ---- gather: butterfly (g, j) takes rows j + s R/16 of column g ----
+    {
+        const Anchor* at = anc + (int64_t)tl * p.nanchor;
+        const int g = tid & (G - 1), j = tid >> LG;
+        const int logB = p.logB;
+        const int half = 1 << (logB - 1);
+        const int m0 = 2 * ((j << LC) + c0 + g);
+        const int d = (m0 & ((1 << logB) - 1)) - half;
+        const int ab0 = m0 >> logB;
+        const int dab = 1 << (LQ + LC + 1 - logB);
+        const float dfs[2] = {(float)d, (float)(d + 1)};
+#pragma unroll
+        for (int s2 = 0; s2 < 16; ++s2) {
+            const int m = m0 + (s2 << (LQ + LC + 1));
+            const int ab = ab0 + s2 * dab;
+            const float4 a4 = __ldg(reinterpret_cast<const float4*>(at + ab));
+            const float q3 = __ldg(&at[ab].q3);
+            const int I = __float_as_int(a4.x) - kRoundBits;
+            const uint32_t dst = smem_u32(sm + pad(g + G * (j + (s2 << LQ))));
+#pragma unroll
+            for (int u = 0; u < 2; ++u) {
+                const float df = dfs[u];
+                const float xr = a4.y - df * fmaf(df, fmaf(df, q3, a4.w), a4.z);
+                const float y = __fadd_rn(xr, kRoundShift);
+                const float fr = __fsub_rn(xr, __fsub_rn(y, kRoundShift));
+                int id = m + u + I + __float_as_int(y);
+                if (!(fabsf(fr) < 0.5f - kGuard)) {
+                    const Anchor a = at[ab];
+                    id = m + u + a.I + off_round_precise(a, d + u);
+                }
+                cp_async4(dst + 4u * u, (unsigned)id < (unsigned)n ? x.f32 + id : x.fillp);
+            }
+        }
+        asm volatile("cp.async.wait_all;" ::: "memory");
+    }
+    __syncthreads();
+    fft_stage<4, 16, true>(sm, LR, 0, LG, 1, G, 0, tw, tid);
+    ws_mid_stage<LG, SyncCTA>(sm, LR, 4, stw, tid);
+    ws_last_stage<RL_LAST, LG>(sm, LC, LM, c0, LNS_LAST, stw + 16, Y + ((int64_t)tl << LM), tid);
+}
+
 // ---- Pass 2 fed by TMA bulk copies ------------------------------------------------------
 // A persistent CTA per SM walks the pass-2 tiles (2 NP rows of C complex = 2^13 values):
 // one producer thread copies the 2 NP rows of tile i + 1 from Y into an unpadded staging
@@ -1075,6 +1145,7 @@ Pass2Fn pick_pass2(const Plan& p)
 namespace {
 cudaError_t ws_attributes(int* nsm);
 cudaError_t p2tma_attributes(int* nsm);
+cudaError_t async_attributes();
 }
 
 // Large dynamic shared memory for the FFT passes, set once per device (a host-side
@@ -1102,6 +1173,7 @@ cudaError_t set_smem_attributes()
     int nsm = 0;
     if (e == cudaSuccess) e = ws_attributes(&nsm);
     if (e == cudaSuccess) e = p2tma_attributes(&nsm);
+    if (e == cudaSuccess) e = async_attributes();
     if (e == cudaSuccess) done[dev] = true;
     return e;
 }
@@ -1154,9 +1226,56 @@ cudaError_t ws_attributes(int* nsm)
 
 }  // namespace
 
+namespace {
+
+using AsyncFn = void (*)(SeriesView, const Anchor*, Plan, const float2*, float2*);
+
+AsyncFn pick_async(const Plan& p)
+{
+#define BPS_PICK(a, b) \
+    if (p.logR == a && p.logC == b) return k_pass1_async<a, b>;
+    BPS_WS_GEOMETRIES(BPS_PICK)
+#undef BPS_PICK
+    return nullptr;
+}
+
+size_t async_smem() { return (size_t)(kWsBufStride + 272) * sizeof(float2); }
+
+cudaError_t async_attributes()
+{
+    static std::mutex mu;
+    static bool done[64] = {};
+    int dev = 0;
+    cudaError_t e = cudaGetDevice(&dev);
+    if (e != cudaSuccess) return e;
+    if (dev < 0 || dev >= 64) return cudaErrorInvalidDevice;
+    std::lock_guard<std::mutex> lk(mu);
+    if (!done[dev]) {
+        const int bytes = (int)async_smem();
+#define BPS_ATTR(a, b) \
+    if (e == cudaSuccess) e = cudaFuncSetAttribute(k_pass1_async<a, b>, cudaFuncAttributeMaxDynamicSharedMemorySize, bytes);
+        BPS_WS_GEOMETRIES(BPS_ATTR)
+#undef BPS_ATTR
+        if (e != cudaSuccess) return e;
+        done[dev] = true;
+    }
+    return cudaSuccess;
+}
+
+}  // namespace
+
 cudaError_t launch_pass1(const SeriesView& x, const Anchor* anc, int nt, const Plan& p,
                          const float2* tw, float2* Y, unsigned long long* status, cudaStream_t s)
 {
+    if (p.p1async && x.f32 && x.fillp) {
+        const AsyncFn f = pick_async(p);
+        if (!f) return cudaErrorInvalidValue;
+        cudaError_t e = async_attributes();
+        if (e != cudaSuccess) return e;
+        dim3 grid((unsigned)(1 << (p.logC - (13 - p.logR))), (unsigned)nt);
+        f<<<grid, 512, async_smem(), s>>>(x, anc, p, tw, Y);
+        return cudaGetLastError();
+    }
     if (p.p1ws) {
         const WsFn f = pick_ws(p);
         if (!f || !status) return cudaErrorInvalidValue;

@@ -6,6 +6,9 @@
   for (R = 2^10, 2^11, 2^12) from 2^21 to 2^25 samples, with FP32 and FP16 series
   storage, and for batches whose tiles outnumber the CTAs (each CTA walks many tiles
   through its two buffers).
+* The one-phase pass 1 with asynchronous gathers (2^13 tiles, two CTAs per SM) gives the
+  oracle's whitened power and candidates for its splits, batched as well as per template;
+  FP16 series, which it does not take, run the one-phase kernel with the same results.
 * The TMA-fed pass 2 (one thread copies the next tile's rows into shared memory with
   bulk copies while the consumer warps transform the current tile) gives the oracle's
   whitened power and candidates for its splits (R, C in 2^10..2^12), alone and combined
@@ -241,3 +244,34 @@ def test_tma_pass2_many_tiles_and_rejects(bps, ctx, orc):
         ctx.search(sid, bid, bps.default_params(log_cols=9, pass2_kind=bps.BPS_PASS2_TMA))
     for i in (sid, bid, sbid):
         ctx.unload(i)
+
+
+@pytest.mark.parametrize("logn,log_cols", [(21, 10), (22, 11), (23, 11), (23, 12), (24, 12)])
+def test_async_pass1_against_oracle(bps, ctx, orc, logn, log_cols):
+    x, ts, bank = _workload(logn, 4800 + logn + log_cols, K=2 if logn <= 23 else 1,
+                            ecc=(log_cols % 2 == 0))
+    n = x.size
+    sid = ctx.load_series(x, ts)
+    bid = ctx.load_bank(bank)
+    prm = bps.default_params(log_cols=log_cols, sigma_thr=5.0, pass1_kind=bps.BPS_PASS1_ASYNC)
+    pw = ctx.whitened_spectrum(sid, bid, 0, len(bank), n, prm)
+    gc, _ = ctx.fetch_candidates(ctx.search(sid, bid, prm))
+    oc, res = oracle_on_gpu_maps(ctx, orc, sid, bid, x, ts, bank, want_arrays=True, sigma=5.0)
+    for t in range(len(bank)):
+        e = pw_close(pw[t], res[t]["Pw"])
+        assert e <= PW_TOL, (t, e)
+    compare_candidates(gc, oc, bps.thresholds(prm, n, len(bank)))
+    if logn == 21:
+        # batched (many CTAs per SM) equals one template per launch; FP16 storage takes the
+        # one-phase kernel and matches it
+        b1 = ctx.fetch_candidates(ctx.search(sid, bid, bps.default_params(
+            log_cols=log_cols, sigma_thr=5.0, pass1_kind=bps.BPS_PASS1_ASYNC, batch=1)))[0]
+        assert np.array_equal(b1, gc)
+        s16 = ctx.load_series(x, ts, dtype=bps.BPS_F16_SCALED)
+        a16 = ctx.fetch_candidates(ctx.search(s16, bid, prm))[0]
+        f16 = ctx.fetch_candidates(ctx.search(s16, bid, bps.default_params(
+            log_cols=log_cols, sigma_thr=5.0, pass1_kind=bps.BPS_PASS1_FUSED)))[0]
+        assert np.array_equal(a16, f16)
+        ctx.unload(s16)
+    ctx.unload(sid)
+    ctx.unload(bid)
