@@ -851,7 +851,7 @@ try {
     if ((rc = run_spectrum(ctx, *s, *b, p, params->mode, template_idx, 1, w, st, tm, cnt + 1))) return rc;
     Thr th;
     for (int L = 0; L < 5; ++L) th.v[L] = INFINITY;
-    CK(launch_harmsum(w.P, w.scale, 1, template_idx, p, th, cd, 1, cnt, so, st));
+    CK(launch_harmsum(w.P, w.scale, 1, template_idx, p, th, cd, 1, cnt, so, w.tile_ctr, st));
     unsigned long long cs[2] = {0, 0};
     CK(cudaMemcpyAsync(s_out, so, sizeof(float) * p.M * p.nlev, cudaMemcpyDeviceToHost, st));
     CK(cudaMemcpyAsync(cs, cnt, sizeof cs, cudaMemcpyDeviceToHost, st));

@@ -199,9 +199,11 @@ cudaError_t launch_whitened(const float* P, const float* scale, int nt, const Pl
 // P holds the whitened spectrum (after launch_block_median); scale unused.  count[0]
 // is the candidate counter, count[1] a status word (bit 0: a bounded wait of the harmonic sum
 // expired; bits 1 and 2 are set by the producer/consumer forms of passes 1 and 2).
+// tile_ctr: a device word the launch zeroes and the CTAs take tiles from.
 cudaError_t launch_harmsum(const float* P, const float* scale, int nt, int64_t tidx0,
                            const Plan& p, const Thr& thr, Cand* cands, int64_t cap,
-                           unsigned long long* count, float* s_out, cudaStream_t s);
+                           unsigned long long* count, float* s_out, unsigned int* tile_ctr,
+                           cudaStream_t s);
 cudaError_t launch_series_stats(const float* x, int64_t n, double* sum, cudaStream_t s);
 // fill = (float)(sum / n) on the device
 cudaError_t launch_fill_from_sum(const double* sum, int64_t n, float* fill, cudaStream_t s);

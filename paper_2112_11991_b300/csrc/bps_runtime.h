@@ -332,6 +332,7 @@ struct Workspace {
     float* P = nullptr;    // power, then the whitened power, in bin order
     float* Pt = nullptr;   // power in pass 2's row-major-by-k1 layout (plan.ptrans)
     float* scale = nullptr;
+    unsigned int* tile_ctr = nullptr;  // the harmonic sum's tile counter
     char* base = nullptr;
 };
 
@@ -361,6 +362,7 @@ inline size_t ws_carve(const Plan& p, int nt, int mode, int anchor_templates, ch
     const size_t pp = align256(sizeof(float) * (size_t)p.M * nt);
     const size_t pt = p.ptrans ? pp : 0;
     const size_t sc = align256(sizeof(float) * (size_t)(p.M >> p.logW) * nt);
+    const size_t tc = 256;
     if (w) {
         char* q = base;
         w->base = base;
@@ -369,9 +371,10 @@ inline size_t ws_carve(const Plan& p, int nt, int mode, int anchor_templates, ch
         w->x = x ? (float*)q : nullptr; q += x;
         w->P = (float*)q; q += pp;
         w->Pt = pt ? (float*)q : nullptr; q += pt;
-        w->scale = (float*)q;
+        w->scale = (float*)q; q += sc;
+        w->tile_ctr = (unsigned int*)q;
     }
-    return a + y + x + pp + pt + sc;
+    return a + y + x + pp + pt + sc + tc;
 }
 
 // Stream-ordered allocation from the context's pool.
@@ -571,7 +574,8 @@ struct Job {
                               w.anc + (t0 - c0) * p.nanchor);
         if (rc) return rc;
         tm.begin(BPS_STAGE_HARMSUM);
-        cudaError_t e = launch_harmsum(w.P, w.scale, cnt, t0, p, th, cands, cap, count, nullptr, st);
+        cudaError_t e = launch_harmsum(w.P, w.scale, cnt, t0, p, th, cands, cap, count, nullptr,
+                                       w.tile_ctr, st);
         tm.end();
         if (e != cudaSuccess)
             return fail(ctx, BPS_ERR_CUDA, "harmonic-sum launch: %s", cudaGetErrorString(e));

@@ -297,8 +297,14 @@ __global__ void k_wait_selftest(int limit, unsigned long long* status)
 // Warp-specialised pipeline: one producer warp copies the H segments of a tile into a
 // ring of kHsStages stages (16-byte-aligned TMA bulk copies, one per lane, completed on
 // the stage's "full" mbarrier); 8 consumer warps sum, threshold and compact, then release
-// the stage on its "empty" mbarrier.  CTAs are persistent over tiles j = blockIdx.x +
-// i gridDim.x.  Two stages (70 KB) let three CTAs share an SM: measured at 2^23, 9.9 us per
+// the stage on its "empty" mbarrier.  CTAs are persistent; the producer takes its tiles
+// from a global counter, kHsChunk consecutive ones per claim, claiming the next chunk while
+// the current one is copied, and passes each index to the consumers with the stage, so all
+// CTAs work on one frontier: a template's whitened spectrum (the segments of a tile reach
+// back to bin k h / 16) stays in the L2 while its tiles are summed.  (With a fixed stride
+// j = blockIdx.x + i gridDim.x the CTAs drifted apart over a 32-template launch, the
+// spectra of several templates were live at once, and 1.7x 2N came from DRAM.)  Two
+// stages (70 KB) let three CTAs share an SM: measured at 2^23, 9.9 us per
 // template against 10.4 with three stages and two CTAs, 18.2 with four stages and one.
 // Every wait is bounded: on expiry the status word is flagged (reported as
 // BPS_ERR_TIMEOUT) and the warp leaves after a bounded drain of its copies in flight.
@@ -307,7 +313,8 @@ constexpr int kHsConsumerWarps = 8;
 constexpr int kHsThreads = 32 * (kHsConsumerWarps + 1);
 constexpr int kHsQN = kHsTile / (32 * kHsConsumerWarps);
 constexpr int kHsStages = 2;
-constexpr int kHsHeader = 128;  // bytes: full and empty barriers
+constexpr int kHsHeader = 128;  // bytes: full and empty barriers, the stages' tile indices
+constexpr int kHsChunk = 4;     // consecutive tiles per claim on the tile counter
 
 template <int NH>
 struct HsGeom {
@@ -325,7 +332,8 @@ __global__ void __launch_bounds__(kHsThreads, 3) k_harmsum(const float* __restri
                                                         int64_t tidx0, Thr thr,
                                                         Cand* __restrict__ cands, int64_t cap,
                                                         unsigned long long* __restrict__ count,
-                                                        float* __restrict__ s_out, int ntiles)
+                                                        float* __restrict__ s_out, int ntiles,
+                                                        unsigned int* __restrict__ tile_ctr)
 {
     using Gm = HsGeom<NH>;
     constexpr int LOGNH = Gm::LOGNH;
@@ -336,10 +344,9 @@ __global__ void __launch_bounds__(kHsThreads, 3) k_harmsum(const float* __restri
     extern __shared__ __align__(128) unsigned char hsm[];
     uint64_t* full = reinterpret_cast<uint64_t*>(hsm);
     uint64_t* empty = full + kHsStages;
+    volatile int* s_tile = reinterpret_cast<volatile int*>(empty + kHsStages);  // -1: no more tiles
     float* seg = reinterpret_cast<float*>(hsm + kHsHeader);
     const int logtpt = p.logM - 10;  // tiles per template = M / 1024
-    const int G = gridDim.x;
-    const int c0 = blockIdx.x;
     const int warp = threadIdx.x >> 5;
     const unsigned lane = threadIdx.x & 31u;
     if (threadIdx.x == 0) {
@@ -359,16 +366,37 @@ __global__ void __launch_bounds__(kHsThreads, 3) k_harmsum(const float* __restri
 #pragma unroll
         for (int hh = 1; hh <= NH; ++hh)
             if (hh == h) soff = Gm::off(hh), slen = Gm::len(hh);
+        // tiles come in chunks of kHsChunk consecutive ones; the next chunk is claimed as soon
+        // as the current one is, so the atomic's round trip overlaps the chunk's copies
+        int jc = 0, jn = 0, sub = 0;
+        if (lane == 0) {
+            jc = (int)atomicAdd(tile_ctr, (unsigned)kHsChunk);
+            jn = (int)atomicAdd(tile_ctr, (unsigned)kHsChunk);
+        }
+        jc = __shfl_sync(0xffffffffu, jc, 0);
         int i = 0;
         for (;; ++i) {
-            const int j = c0 + i * G;
-            if (j >= ntiles) break;
             const int s = i % kHsStages;
             if (i >= kHsStages &&
                 !mbar_wait_parity(&empty[s], (uint32_t)(((i / kHsStages) - 1) & 1))) {
                 if (lane == 0) atomicOr(count + 1, 1ull);
                 break;
             }
+            const int j = jc + sub;
+            if (++sub == kHsChunk) {  // move to the claimed chunk, claim the one after it
+                sub = 0;
+                jc = __shfl_sync(0xffffffffu, jn, 0);
+                if (lane == 0 && jc < ntiles) jn = (int)atomicAdd(tile_ctr, (unsigned)kHsChunk);
+            }
+            if (j >= ntiles) {  // no more tiles: the stage carries the end mark
+                if (lane == 0) {
+                    s_tile[s] = -1;
+                    mbar_arrive(&full[s]);
+                }
+                ++i;
+                break;
+            }
+            if (lane == 0) s_tile[s] = j;
             const int tl = j >> logtpt;
             const int k0 = (j & ((1 << logtpt) - 1)) << 10;
             if (lane == 0) mbar_expect_tx(&full[s], Gm::BYTES);
@@ -393,12 +421,12 @@ __global__ void __launch_bounds__(kHsThreads, 3) k_harmsum(const float* __restri
 #pragma unroll
         for (int s = 0; s < kHsStages; ++s) {
             const int i = i0 + s;
-            const int j = c0 + i * G;
-            if (j >= ntiles) return;
             if (!mbar_wait_parity(&full[s], (uint32_t)((i / kHsStages) & 1))) {
                 if (lane == 0) atomicOr(count + 1, 1ull);
                 return;
             }
+            const int j = s_tile[s];  // written before the producer's arrival on full[s]
+            if (j < 0) return;
             float acc[QN];
             float S[QN][NLEV];
 #pragma unroll
@@ -587,7 +615,7 @@ cudaError_t hs_shape(int& ctas)
 template <int NH>
 cudaError_t launch_hs(const float* P, int nt, int64_t tidx0, const Plan& p, const Thr& thr,
                       Cand* cands, int64_t cap, unsigned long long* count, float* s_out,
-                      cudaStream_t s)
+                      unsigned int* tile_ctr, cudaStream_t s)
 {
     int ctas = 0;
     cudaError_t e = hs_shape<NH>(ctas);
@@ -595,8 +623,10 @@ cudaError_t launch_hs(const float* P, int nt, int64_t tidx0, const Plan& p, cons
     const int64_t ntiles = (p.M / kHsTile) * (int64_t)nt;
     if (ntiles < 1 || ntiles > INT32_MAX) return cudaErrorInvalidValue;
     const int grid = (int)std::min<int64_t>(ntiles, ctas);
+    e = cudaMemsetAsync(tile_ctr, 0, sizeof(unsigned int), s);
+    if (e != cudaSuccess) return e;
     k_harmsum<NH><<<grid, kHsThreads, HsGeom<NH>::SMEM, s>>>(P, p, tidx0, thr, cands, cap, count,
-                                                                  s_out, (int)ntiles);
+                                                                  s_out, (int)ntiles, tile_ctr);
     return cudaGetLastError();
 }
 
@@ -604,15 +634,17 @@ cudaError_t launch_hs(const float* P, int nt, int64_t tidx0, const Plan& p, cons
 
 cudaError_t launch_harmsum(const float* P, const float* scale, int nt, int64_t tidx0,
                            const Plan& p, const Thr& thr, Cand* cands, int64_t cap,
-                           unsigned long long* count, float* s_out, cudaStream_t s)
+                           unsigned long long* count, float* s_out, unsigned int* tile_ctr,
+                           cudaStream_t s)
 {
     (void)scale;
+    if (!tile_ctr) return cudaErrorInvalidValue;
     switch (p.nharm) {
-        case 1: return launch_hs<1>(P, nt, tidx0, p, thr, cands, cap, count, s_out, s);
-        case 2: return launch_hs<2>(P, nt, tidx0, p, thr, cands, cap, count, s_out, s);
-        case 4: return launch_hs<4>(P, nt, tidx0, p, thr, cands, cap, count, s_out, s);
-        case 8: return launch_hs<8>(P, nt, tidx0, p, thr, cands, cap, count, s_out, s);
-        case 16: return launch_hs<16>(P, nt, tidx0, p, thr, cands, cap, count, s_out, s);
+        case 1: return launch_hs<1>(P, nt, tidx0, p, thr, cands, cap, count, s_out, tile_ctr, s);
+        case 2: return launch_hs<2>(P, nt, tidx0, p, thr, cands, cap, count, s_out, tile_ctr, s);
+        case 4: return launch_hs<4>(P, nt, tidx0, p, thr, cands, cap, count, s_out, tile_ctr, s);
+        case 8: return launch_hs<8>(P, nt, tidx0, p, thr, cands, cap, count, s_out, tile_ctr, s);
+        case 16: return launch_hs<16>(P, nt, tidx0, p, thr, cands, cap, count, s_out, tile_ctr, s);
         default: return cudaErrorInvalidValue;
     }
 }
