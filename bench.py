@@ -35,11 +35,14 @@ METRIC = "templates searched/sec at 2^23 samples vs plain GPU form; p50/p99 requ
 UNIT = "templates/s"
 # Algorithmic bytes per template per stage, in units of N (FP32 series):
 #   pass1: series read 4N + packed-complex write 4N; pass2: 4N read + 2N power write;
-#   median: 2N read; harmsum: 2N read.  Whole path (one series read, whitened
-#   spectrum written once and read once): 8N.
+#   median: 2N read + 2N whitened write; harmsum: 2N read.  Whole path (one series read,
+#   whitened spectrum written once and read once): 8N.  With the FFT split into two
+#   passes through device memory the packed intermediate adds a 4N write and a 4N read:
+#   16N, the bound of a two-pass (out-of-core) FFT.
 STAGE_BYTES_PER_N = {"pass1": 8.0, "pass2": 6.0, "median": 4.0, "harmsum": 2.0,
                      "power": 4.0 + 2.0, "anchors": 0.0}
 PATH_BYTES_PER_N = 8.0
+TWO_PASS_BYTES_PER_N = 16.0
 CAND_CAP = 1 << 22
 
 
@@ -655,6 +658,17 @@ def main():
             "alg_bytes_per_launch": alg_bytes, "templates_per_launch": batch,
             "ms_per_launch": per_launch_ms}
     path_gbs = PATH_BYTES_PER_N * n * K * args.steps / (sum(ms) / 1e3) / 1e9
+    two_pass_gbs = TWO_PASS_BYTES_PER_N * n * K * args.steps / (sum(ms) / 1e3) / 1e9
+    # DRAM bytes the four kernels move per template (the committed ncu rows of this launch
+    # shape, when all are current) over the whole step's time
+    per_t = [ncu_traffic(k, "htru_2p%d" % args.logn, 1, geom)
+             for k in ("pass1", "pass2", "median", "harmsum")]
+    path_dram = None
+    if all(v is not None for v in per_t):
+        dram_gbs = sum(per_t) * K * args.steps / (sum(ms) / 1e3) / 1e9
+        path_dram = {"dram_bytes_per_template": sum(per_t), "achieved": dram_gbs, "peak": peak,
+                     "unit": "GB/s", "frac": dram_gbs / peak,
+                     "source": "profiles/traffic.json rows of launch shape " + geom}
     stage_share = {k: v / max(1e-9, sum(stage_ms.values())) for k, v in stage_ms.items()}
 
     cpu = None
@@ -692,6 +706,10 @@ def main():
            "roofline": roof,
            "path_roofline": {"achieved": path_gbs, "peak": peak, "unit": "GB/s",
                              "frac": path_gbs / peak, "alg_bytes_per_template": PATH_BYTES_PER_N * n},
+           "two_pass_roofline": {"achieved": two_pass_gbs, "peak": peak, "unit": "GB/s",
+                                 "frac": two_pass_gbs / peak,
+                                 "alg_bytes_per_template": TWO_PASS_BYTES_PER_N * n},
+           "path_dram": path_dram,
            "stage_ms_per_step": {k: v / args.steps for k, v in stage_ms.items()},
            "stage_share": stage_share,
            "cpu_baseline": cpu, "e2e": e2e, "clocks": clk, "gpu_launches": launches,

@@ -38,6 +38,12 @@ def test_header_symbols_exported(bps):
 def test_struct_layouts(bps):
     assert C.sizeof(bps.bps_candidate) == 16
     assert C.sizeof(bps.bps_template) == 40
+    # bps_search_params as include/bps.h lays it out: eleven int32 fields, one double
+    # and one int64 (at offsets 8 and 24) -> 64 bytes (bps_default_params writes them all)
+    assert C.sizeof(bps.bps_search_params) == 64
+    assert bps.bps_search_params.sigma_thr.offset == 8
+    assert bps.bps_search_params.cand_cap.offset == 24
+    assert bps.bps_search_params.pass2_kind.offset == 60
     assert bps.CAND_DTYPE.itemsize == 16
 
 
@@ -66,7 +72,8 @@ def test_auto_threshold_uses_snmin(bps, orc):
 
 def test_threshold_argument_checks(bps):
     for kw in [dict(nharm_max=3), dict(whiten_block=1000), dict(whiten_block=16),
-               dict(sigma_thr=-1.0), dict(cand_cap=0), dict(mode=7)]:
+               dict(sigma_thr=-1.0), dict(cand_cap=0), dict(mode=7), dict(pass1_kind=4),
+               dict(pass2_kind=3), dict(power_layout=3), dict(log_tile=12)]:
         p = bps.default_params(**kw)
         with pytest.raises(bps.BpsError):
             bps.thresholds(p, 1 << 20, 1)
