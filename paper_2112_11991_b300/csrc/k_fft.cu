@@ -35,6 +35,10 @@ constexpr int kEPT2 = 16;  // elements per thread in pass 2 (one radix-16 butter
 constexpr int kLogTile = 14;  // largest tile (complex values per CTA) of both passes
 
 __device__ __forceinline__ int pad(int i) { return i + (i >> 4); }
+// pad(b + s * st) for a stride st that is a multiple of 16 and b >= 0: the shift of b + 16 m
+// is the shift of b plus m, so the padded address is pad(b) plus s * (st + st / 16) (a
+// constant per element where st is known at compile time; one padding per butterfly)
+__device__ __forceinline__ int pad_step(int st) { return st + (st >> 4); }
 
 __device__ __forceinline__ float2 cmul(float2 a, float2 b)
 {
@@ -179,8 +183,14 @@ __device__ __forceinline__ void fft_stage(float2* buf, int logL, int logNs, int 
         const int base = line * ls + j * es;
         const int qs = Q * es;
         const int lsk = line * skew;
+        if ((qs & 15) == 0) {
+            const float2* src = buf + pad(base) + lsk;
 #pragma unroll
-        for (int s = 0; s < RADIX; ++s) v[i * RADIX + s] = buf[pad(base + s * qs) + lsk];
+            for (int s = 0; s < RADIX; ++s) v[i * RADIX + s] = src[s * pad_step(qs)];
+        } else {
+#pragma unroll
+            for (int s = 0; s < RADIX; ++s) v[i * RADIX + s] = buf[pad(base + s * qs) + lsk];
+        }
         if (logNs > 0) {
             // twiddles W^{k s}, s = 1..RADIX-1, from one table load: W^{2^m} by squaring,
             // the others as products of two lower powers (at most 4 products deep)
@@ -203,9 +213,15 @@ __device__ __forceinline__ void fft_stage(float2* buf, int logL, int logNs, int 
 #pragma unroll
     for (int i = 0; i < BPT; ++i) {
         Radix<LOGRADIX>::dft(v + i * RADIX);
+        if ((nse & 15) == 0) {
+            float2* d = buf + pad(dst[i]) + lskv[i];
 #pragma unroll
-        for (int s = 0; s < RADIX; ++s)
-            buf[pad(dst[i] + s * nse) + lskv[i]] = v[i * RADIX + Radix<LOGRADIX>::out_pos(s)];
+            for (int s = 0; s < RADIX; ++s) d[s * pad_step(nse)] = v[i * RADIX + Radix<LOGRADIX>::out_pos(s)];
+        } else {
+#pragma unroll
+            for (int s = 0; s < RADIX; ++s)
+                buf[pad(dst[i] + s * nse) + lskv[i]] = v[i * RADIX + Radix<LOGRADIX>::out_pos(s)];
+        }
     }
     SYNC::sync();
 }
@@ -292,8 +308,12 @@ __device__ __forceinline__ void pass1_last_stage(const float2* __restrict__ sm, 
         if (BPT <= 2) u0 = twiddle((j2 * (uint32_t)j) & Mm, logM);
         else if (i > 0) u0 = cmul(u0, du);
         float2 v[RL];
+        {
+            // G Ns is a multiple of 16 (Ns >= 16 after the first radix-16 stage)
+            const float2* src = sm + pad(g + G * j);
 #pragma unroll
-        for (int s = 0; s < RL; ++s) v[s] = sm[pad(g + G * (j + s * Ns))];
+            for (int s = 0; s < RL; ++s) v[s] = src[s * pad_step(G * Ns)];
+        }
         {
             float2 w[RL];
             w[1] = __ldg(tw + (j << twshift));
@@ -403,8 +423,10 @@ __global__ void __launch_bounds__(512, 1) k_pass1(SeriesView x, const Anchor* __
             gather_f16_butterfly(x, n, id, v);
         }
         Radix<4>::dft(v);
+        // pad(g + 16 G j + G s) = pad(g + 16 G j) + G s + (G s) / 16, as g < G
+        float2* d = sm + pad(g + 16 * G * j);
 #pragma unroll
-        for (int s = 0; s < 16; ++s) sm[pad(g + G * (16 * j + s))] = v[Radix<4>::out_pos(s)];
+        for (int s = 0; s < 16; ++s) d[G * s + ((G * s) >> 4)] = v[Radix<4>::out_pos(s)];
     }
     __syncthreads();
     int logNs = 4;
@@ -803,10 +825,10 @@ __device__ __forceinline__ void pass2_tile(const float2* __restrict__ src, int t
             for (int s = 0; s < 16; ++s) v[s] = ld_once(rs + (s << logQ));
         }
         Radix<4>::dft(v);
-        const int base = line * C + 16 * j;
-        const int lsk = line * skew;
+        // base is a multiple of 16, so pad(base + s) = pad(base) + s for s < 16
+        float2* d = sm + pad(line * C + 16 * j) + line * skew;
 #pragma unroll
-        for (int s = 0; s < 16; ++s) sm[pad(base + s) + lsk] = v[Radix<4>::out_pos(s)];
+        for (int s = 0; s < 16; ++s) d[s] = v[Radix<4>::out_pos(s)];
     }
     SYNC::sync();
     {
@@ -833,6 +855,13 @@ __device__ __forceinline__ void pass2_tile(const float2* __restrict__ src, int t
                    (k1 & (NP - 1));
         };
         static_assert(kEPT2 % 2 == 0, "items per thread");
+        // a thread's items share ql and step k2 by S = nthr / NP = C / 8; when S is a multiple
+        // of 16 the padded addresses of its low and mirror elements step by pad_step(S)
+        const int S = nthr >> logNP;
+        const bool sstep = (S & 15) == 0;
+        const int ql0 = tid & (NP - 1), k20 = tid >> logNP;
+        const int lo_base = pad(ql0 * C + k20) + ql0 * skew;
+        const int hi_base = pad((NP + ql0) * C + (C - 1 - k20)) + (NP + ql0) * skew;
 #pragma unroll
         for (int r = 0; r < kEPT2 / 2; ++r) {  // items = NP C = (kEPT2 / 2) nthr
             const int it = tid + r * nthr;
@@ -843,8 +872,9 @@ __device__ __forceinline__ void pass2_tile(const float2* __restrict__ src, int t
             float pa, pb;
             if (q != 0) {
                 const float2 w = cmul(s_wq[ql], __ldg(tw + (k2 << twsh)));
-                power_pair(sm[pad(lowl * C + k2) + lo0], sm[pad(highl * C + (C - 1 - k2)) + hi0], w,
-                           pa, pb);
+                const int la = sstep ? lo_base + r * pad_step(S) : pad(lowl * C + k2) + lo0;
+                const int ha = sstep ? hi_base - r * pad_step(S) : pad(highl * C + (C - 1 - k2)) + hi0;
+                power_pair(sm[la], sm[ha], w, pa, pb);
                 Pt[at_(q, k2)] = pa;
                 Pt[at_(R - q, C - 1 - k2)] = pb;
             } else {
@@ -877,6 +907,10 @@ __device__ __forceinline__ void pass2_tile(const float2* __restrict__ src, int t
     const int twsh = 12 - logC;
     const int lowl = ql, highl = NP + ql;
     const int lo0 = lowl * skew, hi0 = highl * skew;
+    const int S = nthr >> logNP;  // k2 step between a thread's items
+    const bool sstep = (S & 15) == 0;
+    const int lo_base = pad(lowl * C + (tid >> logNP)) + lo0;
+    const int hi_base = pad(highl * C + (C - 1 - (tid >> logNP))) + hi0;
 #pragma unroll
     for (int r = 0; r < kEPT2 / 2; ++r) {  // items = NP C = (kEPT2 / 2) nthr
         const int it = tid + r * nthr;
@@ -885,8 +919,9 @@ __device__ __forceinline__ void pass2_tile(const float2* __restrict__ src, int t
             const int64_t k = q + ((int64_t)k2 << logR);
             const float2 w = cmul(wq, __ldg(tw + (k2 << twsh)));
             float pa, pb;
-            power_pair(sm[pad(lowl * C + k2) + lo0], sm[pad(highl * C + (C - 1 - k2)) + hi0], w,
-                       pa, pb);
+            const int la = sstep ? lo_base + r * pad_step(S) : pad(lowl * C + k2) + lo0;
+            const int ha = sstep ? hi_base - r * pad_step(S) : pad(highl * C + (C - 1 - k2)) + hi0;
+            power_pair(sm[la], sm[ha], w, pa, pb);
             Pt[k] = pa;
             Pt[M - k] = pb;
         } else {
