@@ -242,16 +242,38 @@ __global__ void __launch_bounds__(32 * kMedCols) k_median_warp_t(const float* __
     constexpr int LCH = kLogMedCols + LOGT;  // log2 of the floats of one group's kMedCols columns
     const float* g0 = src + ((int64_t)(k20 >> kLogMedCols) << (p.logR + kLogMedCols)) +
                       ((int64_t)(q0 >> LOGT) << LCH);
-#pragma unroll 4
-    for (int i = threadIdx.x; i < (W * kMedCols) / 4; i += 32 * kMedCols) {
-        const int f = 4 * i;
-        const int gi = f >> LCH, o = f & ((1 << LCH) - 1);
-        const float4 v = __ldg(reinterpret_cast<const float4*>(g0 + f));
-        const float e[4] = {v.x, v.y, v.z, v.w};
+    // thread t loads float4 t + 256 i (i < W / 32): floats f = 4 t + 1024 i.  1024 is a
+    // multiple of the group size 2^LCH, so the place in the group (o) is the same for all
+    // of a thread's loads and the group index steps by 1024 / 2^LCH: each element's tile
+    // slot is the thread's first slot plus a constant per i.
+    constexpr int FSTEP = 4 * 32 * kMedCols;
+    static_assert(FSTEP % (1 << LCH) == 0, "load step is a whole number of groups");
+    if (W * kMedCols >= FSTEP) {
+        const int f0 = 4 * (int)threadIdx.x;
+        const int o = f0 & ((1 << LCH) - 1);
+        uint32_t* trow = tile + ((f0 >> LCH) << LOGT) * TS;
+        int slot[4];
 #pragma unroll
-        for (int u = 0; u < 4; ++u) {
-            const int c = (o + u) >> LOGT, r = (gi << LOGT) + ((o + u) & ((1 << LOGT) - 1));
-            tile[r * TS + c] = __float_as_uint(e[u]);
+        for (int u = 0; u < 4; ++u) slot[u] = ((o + u) & ((1 << LOGT) - 1)) * TS + ((o + u) >> LOGT);
+#pragma unroll 4
+        for (int i = 0; i < (W * kMedCols) / FSTEP; ++i) {
+            const float4 v = __ldg(reinterpret_cast<const float4*>(g0 + f0 + i * FSTEP));
+            const float e[4] = {v.x, v.y, v.z, v.w};
+            uint32_t* tr = trow + i * ((FSTEP >> LCH) << LOGT) * TS;
+#pragma unroll
+            for (int u = 0; u < 4; ++u) tr[slot[u]] = __float_as_uint(e[u]);
+        }
+    } else {  // W < 128: fewer float4s than threads
+        for (int i = threadIdx.x; i < (W * kMedCols) / 4; i += 32 * kMedCols) {
+            const int f = 4 * i;
+            const int gi = f >> LCH, o = f & ((1 << LCH) - 1);
+            const float4 v = __ldg(reinterpret_cast<const float4*>(g0 + f));
+            const float e[4] = {v.x, v.y, v.z, v.w};
+#pragma unroll
+            for (int u = 0; u < 4; ++u) {
+                const int c = (o + u) >> LOGT, r = (gi << LOGT) + ((o + u) & ((1 << LOGT) - 1));
+                tile[r * TS + c] = __float_as_uint(e[u]);
+            }
         }
     }
     __syncthreads();

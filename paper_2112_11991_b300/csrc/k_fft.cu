@@ -330,11 +330,11 @@ __device__ __forceinline__ void pass1_last_stage(const float2* __restrict__ sm, 
         u[0] = u0;
 #pragma unroll
         for (int s = 1; s < RL; ++s) u[s] = cmul(u[0], st[s]);
+        // outputs k1 = j + s Ns: row k1 of Y, column j2
+        float2* yb = Yt + ((int64_t)j << logC) + j2;
 #pragma unroll
-        for (int s = 0; s < RL; ++s) {
-            const int k1 = j + s * Ns;
-            __stcs(Yt + ((int64_t)k1 << logC) + j2, cmul(v[Radix<LOGR_LAST>::out_pos(s)], u[s]));
-        }
+        for (int s = 0; s < RL; ++s)
+            __stcs(yb + ((int64_t)(s * Ns) << logC), cmul(v[Radix<LOGR_LAST>::out_pos(s)], u[s]));
     }
 }
 
@@ -862,6 +862,11 @@ __device__ __forceinline__ void pass2_tile(const float2* __restrict__ src, int t
         const int ql0 = tid & (NP - 1), k20 = tid >> logNP;
         const int lo_base = pad(ql0 * C + k20) + ql0 * skew;
         const int hi_base = pad((NP + ql0) * C + (C - 1 - k20)) + (NP + ql0) * skew;
+        // with S a multiple of 8 the items' output offsets step by S / 8 column blocks of
+        // 8 R floats (k2 mod 8 and the row part are the same for all of a thread's items)
+        const bool astep = (S & ((1 << LB) - 1)) == 0;
+        const int64_t astride = (int64_t)(S >> LB) << (logR + LB);
+        const int64_t a_lo = at_(q0 + ql0, k20), a_hi = at_(R - (q0 + ql0), C - 1 - k20);
 #pragma unroll
         for (int r = 0; r < kEPT2 / 2; ++r) {  // items = NP C = (kEPT2 / 2) nthr
             const int it = tid + r * nthr;
@@ -875,8 +880,8 @@ __device__ __forceinline__ void pass2_tile(const float2* __restrict__ src, int t
                 const int la = sstep ? lo_base + r * pad_step(S) : pad(lowl * C + k2) + lo0;
                 const int ha = sstep ? hi_base - r * pad_step(S) : pad(highl * C + (C - 1 - k2)) + hi0;
                 power_pair(sm[la], sm[ha], w, pa, pb);
-                Pt[at_(q, k2)] = pa;
-                Pt[at_(R - q, C - 1 - k2)] = pb;
+                Pt[astep ? a_lo + r * astride : at_(q, k2)] = pa;
+                Pt[astep ? a_hi - r * astride : at_(R - q, C - 1 - k2)] = pb;
             } else {
                 if (k2 <= (C >> 1)) {  // row 0: bins R k2 and M - R k2 = R (C - k2)
                     power_pair(sm[pad(k2) + lo0], sm[pad((C - k2) & (C - 1)) + lo0],
