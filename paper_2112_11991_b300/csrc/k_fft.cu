@@ -387,6 +387,71 @@ __device__ __forceinline__ void pass1_indices(const Anchor* __restrict__ at, int
     }
 }
 
+// The two first-stage butterflies (col, j) and (col + 1, j) of an even column col, FP32
+// series: rows j + s R/16 (s < 16) hold samples 2 (row C + col) + u, u < 4, four
+// consecutive samples inside one anchor block (2 col is a multiple of 4), so each row's
+// anchor is loaded once for all four; the index map of each sample is pass1_indices'.
+// Rows go in two halves of eight (32 indices, then their 32 gathers), so all 64 gathers
+// are in flight before either butterfly is transformed.  v0 gets column col + swp, v1
+// column col + 1 - swp (swp = 0 or 1: the caller's store order).
+__device__ __forceinline__ void pass1_gather_colpair(const SeriesView& x, int n, const Anchor* __restrict__ at,
+                                                     int logB, int logQ, int logC, int col, int j, int swp,
+                                                     float2 (&v0)[16], float2 (&v1)[16])
+{
+    const int half = 1 << (logB - 1);
+    const int m0 = 2 * ((j << logC) + col);
+    const int d = (m0 & ((1 << logB) - 1)) - half;
+    const int ab0 = m0 >> logB;
+    const int dab = 1 << (logQ + logC + 1 - logB);
+    // slot u holds sample m0 + (u xor 2 swp)
+    int uo[4];
+    float dfs[4];
+#pragma unroll
+    for (int u = 0; u < 4; ++u) {
+        uo[u] = u ^ (2 * swp);
+        dfs[u] = (float)(d + uo[u]);
+    }
+#pragma unroll
+    for (int h8 = 0; h8 < 2; ++h8) {
+        int id[32];
+        unsigned pm = 0;
+#pragma unroll
+        for (int r = 0; r < 8; ++r) {
+            const int s = 8 * h8 + r;
+            const int m = m0 + (s << (logQ + logC + 1));
+            const int ab = ab0 + s * dab;
+            const float4 a4 = __ldg(reinterpret_cast<const float4*>(at + ab));
+            const float q3 = __ldg(&at[ab].q3);
+            const int I = __float_as_int(a4.x) - kRoundBits;
+#pragma unroll
+            for (int u = 0; u < 4; ++u) {
+                const float df = dfs[u];
+                const float xr = a4.y - df * fmaf(df, fmaf(df, q3, a4.w), a4.z);
+                const float y = __fadd_rn(xr, kRoundShift);
+                const float fr = __fsub_rn(xr, __fsub_rn(y, kRoundShift));
+                if (!(fabsf(fr) < 0.5f - kGuard)) pm |= 1u << (4 * r + u);
+                id[4 * r + u] = m + uo[u] + I + __float_as_int(y);
+            }
+        }
+        if (pm) {
+#pragma unroll
+            for (int q = 0; q < 32; ++q) {
+                if (pm & (1u << q)) {
+                    const int s = 8 * h8 + (q >> 2), u = uo[q & 3];
+                    const int m = m0 + (s << (logQ + logC + 1));
+                    const Anchor a = at[ab0 + s * dab];
+                    id[q] = m + u + a.I + off_round_precise(a, d + u);
+                }
+            }
+        }
+#pragma unroll
+        for (int r = 0; r < 8; ++r) {
+            v0[8 * h8 + r] = gather_pair_f32(x, n, id[4 * r], id[4 * r + 1]);
+            v1[8 * h8 + r] = gather_pair_f32(x, n, id[4 * r + 2], id[4 * r + 3]);
+        }
+    }
+}
+
 // LR, LC, LG >= 0: log R, log C, log G fixed at compile time (index arithmetic folds
 // into constants); -1: taken from the plan.
 template <int LR, int LC, int LG>
@@ -408,6 +473,28 @@ __global__ void __launch_bounds__(512, 1) k_pass1(SeriesView x, const Anchor* __
     const int n = 2 << logM;
     const Anchor* at = anc + (int64_t)tl * p.nanchor;
     constexpr int BPT1 = kEPT / 16;
+    static_assert(BPT1 == 2, "two first-stage butterflies per thread");
+    if (G >= 2 && x.f32) {
+        // thread t: butterfly j = t / (G/2) of the column pair g, g + 1 (g = 2 (t mod G/2)).
+        // Element (g', j) of stage row s sits at pad(g' + 16 G j) + G s + (G s) / 16 (g' < G),
+        // bank pair (g' + 17 G j) mod 16: the rows j of a warp reach only 16 / G of them for
+        // G < 16, so lanes whose bit log2(16 / G) of j is set write their odd column first;
+        // each store instruction then hits every bank pair twice (no conflict beyond the
+        // two wavefronts 32 float2 need).
+        const int g = 2 * ((int)threadIdx.x & ((G >> 1) - 1));
+        const int j = (int)threadIdx.x >> (logG - 1);
+        const int swp = (j >> (logG < 4 ? 4 - logG : 0)) & 1;
+        float2 v0[16], v1[16];
+        pass1_gather_colpair(x, n, at, p.logB, logQ, logC, c0 + g, j, swp, v0, v1);
+        Radix<4>::dft(v0);
+        float2* d0 = sm + pad(g + swp + 16 * G * j);
+#pragma unroll
+        for (int s = 0; s < 16; ++s) d0[G * s + ((G * s) >> 4)] = v0[Radix<4>::out_pos(s)];
+        Radix<4>::dft(v1);
+        float2* d1 = sm + pad(g + 1 - swp + 16 * G * j);
+#pragma unroll
+        for (int s = 0; s < 16; ++s) d1[G * s + ((G * s) >> 4)] = v1[Radix<4>::out_pos(s)];
+    } else {
 #pragma unroll 1
     for (int i = 0; i < BPT1; ++i) {
         const int b = threadIdx.x + i * nthr;
@@ -427,6 +514,7 @@ __global__ void __launch_bounds__(512, 1) k_pass1(SeriesView x, const Anchor* __
         float2* d = sm + pad(g + 16 * G * j);
 #pragma unroll
         for (int s = 0; s < 16; ++s) d[G * s + ((G * s) >> 4)] = v[Radix<4>::out_pos(s)];
+    }
     }
     __syncthreads();
     int logNs = 4;
