@@ -288,7 +288,8 @@ def test_autotune_choice_and_invariance(bps, ctx, w1):
                                                                         batch=8)))
     best, ms = ctx.autotune(sid, bid, bps.default_params(), sample_templates=8)
     assert best.log_tile in (13, 14) and best.log_tile2 in (13, 14) and best.batch in (4, 8)
-    assert best.log_cols in (9, 10, 11)  # 2^18 samples: the default split (10) or a neighbour
+    # 2^18 samples: the default split (10) or one the autotuner also tries (-1, +1, +2)
+    assert best.log_cols in (9, 10, 11, 12)
     assert ms > 0
     got, _ = ctx.fetch_candidates(ctx.search(sid, bid, bps.default_params()))  # uses the choice
     # the same launch shape given explicitly computes the same floats
