@@ -387,13 +387,14 @@ __device__ __forceinline__ void pass1_indices(const Anchor* __restrict__ at, int
     }
 }
 
-// The two first-stage butterflies (col, j) and (col + 1, j) of an even column col, FP32
-// series: rows j + s R/16 (s < 16) hold samples 2 (row C + col) + u, u < 4, four
+// The two first-stage butterflies (col, j) and (col + 1, j) of an even column col
+// (F16: FP16 series with block scales, else FP32): rows j + s R/16 (s < 16) hold samples 2 (row C + col) + u, u < 4, four
 // consecutive samples inside one anchor block (2 col is a multiple of 4), so each row's
 // anchor is loaded once for all four; the index map of each sample is pass1_indices'.
 // Rows go in two halves of eight (32 indices, then their 32 gathers), so all 64 gathers
 // are in flight before either butterfly is transformed.  v0 gets column col + swp, v1
 // column col + 1 - swp (swp = 0 or 1: the caller's store order).
+template <bool F16>
 __device__ __forceinline__ void pass1_gather_colpair(const SeriesView& x, int n, const Anchor* __restrict__ at,
                                                      int logB, int logQ, int logC, int col, int j, int swp,
                                                      float2 (&v0)[16], float2 (&v1)[16])
@@ -444,17 +445,29 @@ __device__ __forceinline__ void pass1_gather_colpair(const SeriesView& x, int n,
                 }
             }
         }
+        if (!F16) {
 #pragma unroll
-        for (int r = 0; r < 8; ++r) {
-            v0[8 * h8 + r] = gather_pair_f32(x, n, id[4 * r], id[4 * r + 1]);
-            v1[8 * h8 + r] = gather_pair_f32(x, n, id[4 * r + 2], id[4 * r + 3]);
+            for (int r = 0; r < 8; ++r) {
+                v0[8 * h8 + r] = gather_pair_f32(x, n, id[4 * r], id[4 * r + 1]);
+                v1[8 * h8 + r] = gather_pair_f32(x, n, id[4 * r + 2], id[4 * r + 3]);
+            }
+        } else {
+            // FP16 samples: the 32 loads (and block scales) first, then the conversions
+            float2 w[16];
+            gather_f16_butterfly(x, n, id, w);
+#pragma unroll
+            for (int r = 0; r < 8; ++r) {
+                v0[8 * h8 + r] = w[2 * r];
+                v1[8 * h8 + r] = w[2 * r + 1];
+            }
         }
     }
 }
 
 // LR, LC, LG >= 0: log R, log C, log G fixed at compile time (index arithmetic folds
-// into constants); -1: taken from the plan.
-template <int LR, int LC, int LG>
+// into constants); -1: taken from the plan.  F16: the series is stored FP16 with block
+// scales (a separate instantiation, so each storage form gets its own register allocation).
+template <int LR, int LC, int LG, bool F16>
 __global__ void __launch_bounds__(512, 1) k_pass1(SeriesView x, const Anchor* __restrict__ anc,
                                                   Plan p, const float2* __restrict__ tw,
                                                   float2* __restrict__ Y)
@@ -474,7 +487,7 @@ __global__ void __launch_bounds__(512, 1) k_pass1(SeriesView x, const Anchor* __
     const Anchor* at = anc + (int64_t)tl * p.nanchor;
     constexpr int BPT1 = kEPT / 16;
     static_assert(BPT1 == 2, "two first-stage butterflies per thread");
-    if (G >= 2 && x.f32) {
+    if (G >= 2) {
         // thread t: butterfly j = t / (G/2) of the column pair g, g + 1 (g = 2 (t mod G/2)).
         // Element (g', j) of stage row s sits at pad(g' + 16 G j) + G s + (G s) / 16 (g' < G),
         // bank pair (g' + 17 G j) mod 16: the rows j of a warp reach only 16 / G of them for
@@ -485,7 +498,7 @@ __global__ void __launch_bounds__(512, 1) k_pass1(SeriesView x, const Anchor* __
         const int j = (int)threadIdx.x >> (logG - 1);
         const int swp = (j >> (logG < 4 ? 4 - logG : 0)) & 1;
         float2 v0[16], v1[16];
-        pass1_gather_colpair(x, n, at, p.logB, logQ, logC, c0 + g, j, swp, v0, v1);
+        pass1_gather_colpair<F16>(x, n, at, p.logB, logQ, logC, c0 + g, j, swp, v0, v1);
         Radix<4>::dft(v0);
         float2* d0 = sm + pad(g + swp + 16 * G * j);
 #pragma unroll
@@ -503,7 +516,7 @@ __global__ void __launch_bounds__(512, 1) k_pass1(SeriesView x, const Anchor* __
         int id[32];
         pass1_indices(at, p.logB, logQ, logC, c0 + g, j, id);
         float2 v[16];
-        if (x.f32) {
+        if (!F16) {
 #pragma unroll
             for (int s = 0; s < 16; ++s) v[s] = gather_pair_f32(x, n, id[2 * s], id[2 * s + 1]);
         } else {
@@ -1250,13 +1263,14 @@ using Pass2Fn = void (*)(const float2*, Plan, const float2*, float*);
     X(12, 11, 2) X(12, 12, 0) X(12, 12, 1) X(11, 11, 1) X(11, 11, 2) X(11, 12, 0) X(11, 12, 1) \
     X(-1, -1, -1)
 
-Pass1Fn pick_pass1(const Plan& p)
+Pass1Fn pick_pass1(const Plan& p, bool f16)
 {
-#define BPS_PICK(a, b, c) \
-    if ((a < 0) || (p.logR == a && p.logC == b && p.logG == c)) return k_pass1<a, b, c>;
+#define BPS_PICK(a, b, c)                                                  \
+    if ((a < 0) || (p.logR == a && p.logC == b && p.logG == c))            \
+        return f16 ? k_pass1<a, b, c, true> : k_pass1<a, b, c, false>;
     BPS_PASS1_GEOMETRIES(BPS_PICK)
 #undef BPS_PICK
-    return k_pass1<-1, -1, -1>;
+    return f16 ? k_pass1<-1, -1, -1, true> : k_pass1<-1, -1, -1, false>;
 }
 
 Pass2Fn pick_pass2(const Plan& p)
@@ -1288,9 +1302,11 @@ cudaError_t set_smem_attributes()
     std::lock_guard<std::mutex> lk(mu);
     if (done[dev]) return cudaSuccess;
     const int bytes = (int)tile_smem(kLogTile);
-#define BPS_ATTR(a, b, c) \
-    if (e == cudaSuccess)  \
-        e = cudaFuncSetAttribute(k_pass1<a, b, c>, cudaFuncAttributeMaxDynamicSharedMemorySize, bytes);
+#define BPS_ATTR(a, b, c)                                                                               \
+    if (e == cudaSuccess)                                                                                \
+        e = cudaFuncSetAttribute(k_pass1<a, b, c, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, bytes); \
+    if (e == cudaSuccess)                                                                                \
+        e = cudaFuncSetAttribute(k_pass1<a, b, c, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, bytes);
     BPS_PASS1_GEOMETRIES(BPS_ATTR)
 #undef BPS_ATTR
 #define BPS_ATTR(a, b, c) \
@@ -1420,7 +1436,7 @@ cudaError_t launch_pass1(const SeriesView& x, const Anchor* anc, int nt, const P
     cudaError_t e = set_smem_attributes();
     if (e != cudaSuccess) return e;
     dim3 grid((unsigned)(1 << (p.logC - p.logG)), (unsigned)nt);
-    pick_pass1(p)<<<grid, (1 << logt) / kEPT, tile_smem(logt), s>>>(x, anc, p, tw, Y);
+    pick_pass1(p, x.f16 != nullptr)<<<grid, (1 << logt) / kEPT, tile_smem(logt), s>>>(x, anc, p, tw, Y);
     return cudaGetLastError();
 }
 
