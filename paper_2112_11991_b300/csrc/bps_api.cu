@@ -255,8 +255,9 @@ try {
     Bank b;
     b.K = count;
     b.h.assign(t, t + count);
+    const std::vector<DevTemplate> dt = dev_templates(t, count);
     CK(cudaMalloc((void**)&b.d, sizeof(DevTemplate) * count));
-    CK(cudaMemcpy(b.d, t, sizeof(DevTemplate) * count, cudaMemcpyHostToDevice));
+    CK(cudaMemcpy(b.d, dt.data(), sizeof(DevTemplate) * count, cudaMemcpyHostToDevice));
     const int64_t id = ctx->next_id++;
     ctx->banks[id] = std::move(b);
     *bank_id = id;

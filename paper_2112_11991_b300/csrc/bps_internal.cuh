@@ -7,9 +7,14 @@
 
 namespace bps {
 
-// One orbital template, same layout as the public bps_template (App. A, BT model).
+// One orbital template on the device (App. A, BT model): the public bps_template's five
+// parameters followed by per-template constants of the anchor kernel, computed once on the
+// host in FP64 (dev_template in bps_runtime.h): Omega = 2 pi / P_orb, sin and cos of the
+// periastron longitude, sqrt(1 - e^2), and the zero offset's delay Delta_R(0) (Kepler's
+// equation at M = alpha; Algorithm 1 subtracts it so that idx_0 = 0).
 struct DevTemplate {
     double porb, tau, phi, omega, ecc;
+    double om, sw, cw, rt, delta0;
 };
 
 // Per-anchor constants of the index map (Algorithm 1), evaluated in FP64 at the
@@ -64,6 +69,7 @@ struct Plan {
                     // series with a device fill value; the one-phase kernel otherwise)
     int p2tma;      // 1: pass 2 fed by TMA bulk copies of its rows (persistent, 2^13 tiles)
     double tsamp;
+    double inv_tsamp;  // 1 / tsamp
 };
 
 // Four-step splits (log R, log C) the warp-specialised pass 1 is built for (2^13-complex

@@ -32,6 +32,7 @@
 
 #include "../../include/bps.h"
 #include "bps_internal.cuh"
+#include "dev_template.h"
 
 namespace bps {
 
@@ -118,6 +119,7 @@ try {
     p.lognh = 0;
     p.nlev = 1;
     p.tsamp = tsamp_s;
+    p.inv_tsamp = 1.0 / tsamp_s;
     const double K = t.tau_lts / tsamp_s;
     const double g = (2.0 * M_PI / t.porb_s) * tsamp_s / (1.0 - t.ecc);
     const int logB = plan_anchor_block(K * g, K * g * g, K * g * g * g * g, logn);
@@ -144,12 +146,7 @@ try {
     float* P = (float*)(base + a_tw + a_tm + a_an + a_y);
     float* scale = (float*)(base + a_tw + a_tm + a_an + a_y + a_p);
 
-    DevTemplate tv;
-    tv.porb = t.porb_s;
-    tv.tau = t.tau_lts;
-    tv.phi = t.phi_rad;
-    tv.omega = t.omega_rad;
-    tv.ecc = t.ecc;
+    const DevTemplate tv = rt::dev_template(t);
     SeriesView v;
     v.f32 = d_series;
     v.f16 = nullptr;

@@ -20,6 +20,7 @@
 
 #include "../../include/bps.h"
 #include "bps_internal.cuh"
+#include "dev_template.h"
 
 namespace bps {
 namespace rt {
@@ -43,6 +44,7 @@ struct Bank {
     DevTemplate* d = nullptr;
     std::vector<bps_template> h;
 };
+
 
 struct Request {
     int64_t series = 0, bank = 0, K = 0;
@@ -283,6 +285,7 @@ inline int make_plan(bps_ctx* ctx, const Series& s, const Bank& b, const bps_sea
     p.lognh = ilog2(pr.nharm_max);
     p.nlev = p.lognh + 1;
     p.tsamp = s.tsamp;
+    p.inv_tsamp = 1.0 / s.tsamp;
     // per template: K = tau/t_s, g = Omega t_s / (1 - e) (bound on dE/dsample)
     double kg1 = 0.0, kg2 = 0.0, kg4 = 0.0, Kmax = 0.0, gmax = 0.0;
     for (const auto& t : b.h) {

@@ -50,6 +50,7 @@ struct SReq {
     double tsamp = 0;
     int dtype = BPS_F32;
     std::vector<bps_template> bank;
+    std::vector<DevTemplate> dbank;  // device form of the bank (kept until its copy is done)
     bps_search_params prm;
     size_t bytes = 0;
     int slot = -1;
@@ -302,6 +303,7 @@ bool admit_one(bps_server* srv, SReq& q, int slot)
     q.s.owned = true;
     q.b.K = (int64_t)q.bank.size();
     q.b.h = q.bank;
+    q.dbank = dev_templates(q.bank.data(), (int64_t)q.bank.size());
     if (q.ser) {
         SSeries& ser = *q.ser;
         ser.last_use = now_s();
@@ -314,7 +316,7 @@ bool admit_one(bps_server* srv, SReq& q, int slot)
         chk(pool_alloc(srv->ctx, (void**)&q.d_cands, sizeof(Cand) * (size_t)q.prm.cand_cap, st));
         chk(pool_alloc(srv->ctx, (void**)&q.d_count, 2 * sizeof(unsigned long long), st));
         if (ok) {
-            chk(cudaMemcpyAsync(q.b.d, q.bank.data(), sizeof(DevTemplate) * q.bank.size(),
+            chk(cudaMemcpyAsync(q.b.d, q.dbank.data(), sizeof(DevTemplate) * q.bank.size(),
                                 cudaMemcpyHostToDevice, st));
             chk(cudaMemsetAsync(q.d_count, 0, 2 * sizeof(unsigned long long), st));
             chk(cudaEventRecord(q.ev, st));
@@ -340,7 +342,7 @@ bool admit_one(bps_server* srv, SReq& q, int slot)
     chk(pool_alloc(srv->ctx, (void**)&q.d_count, 2 * sizeof(unsigned long long), st));
     if (ok) {
         chk(cudaMemcpyAsync(src, q.h_series, 4 * n, cudaMemcpyHostToDevice, st));
-        chk(cudaMemcpyAsync(q.b.d, q.bank.data(), sizeof(DevTemplate) * q.bank.size(),
+        chk(cudaMemcpyAsync(q.b.d, q.dbank.data(), sizeof(DevTemplate) * q.bank.size(),
                             cudaMemcpyHostToDevice, st));
         chk(cudaMemsetAsync(q.d_sum, 0, sizeof(double), st));
         chk(cudaMemsetAsync(q.d_count, 0, 2 * sizeof(unsigned long long), st));

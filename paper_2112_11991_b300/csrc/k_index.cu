@@ -4,10 +4,11 @@
 // Anchor kernel (App. A.1, Algorithm 1; Kepler's equation, Sec. 2.1; BT Roemer
 // delay, App. A): for every template and every anchor block of B samples it
 // reduces the mean anomaly M = Omega t_c + alpha in FP64, solves Kepler's
-// equation by FP64 Newton iteration, evaluates the BT delay and the zero offset
-// t_0 = Delta_R(0)/t_s, and stores the FP32 constants the per-sample
-// evaluation (index_map.cuh) needs.  FP64 work is N/B Kepler solves per
-// template (B is chosen by the planner, typically 4096-16384 samples).
+// equation by FP64 Newton iteration, evaluates the BT delay against the zero
+// offset Delta_R(0) (computed per template on the host, dev_template.h), and
+// stores the FP32 constants the per-sample evaluation (index_map.cuh) needs.
+// FP64 work is N/B Kepler solves per template (B is chosen by the planner,
+// typically 4096-16384 samples).
 #include <cmath>
 
 #include "bps_internal.cuh"
@@ -19,68 +20,65 @@ namespace {
 
 constexpr double kTwoPi = 6.283185307179586476925286766559;
 
+constexpr double kInvTwoPi = 0.15915494309189533576888376337251;
+
+// x mod 2 pi in [0, 2 pi) (the quotient by a product with 1 / (2 pi): a quotient one off at
+// a boundary is put right by the two corrections)
 __device__ double reduce_2pi(double x)
 {
-    double r = x - kTwoPi * floor(x / kTwoPi);
+    double r = x - kTwoPi * floor(x * kInvTwoPi);
     if (r < 0.0) r += kTwoPi;
     if (r >= kTwoPi) r -= kTwoPi;
     return r;
 }
 
-// Kepler's equation E - e sin E = M by Newton iteration from E0 = M + e sin M.
-__device__ double kepler64(double M, double e)
-{
-    double E = M + e * sin(M);
-    for (int it = 0; it < 40; ++it) {
-        double s, c;
-        sincos(E, &s, &c);
-        const double dE = (E - e * s - M) / (1.0 - e * c);
-        E -= dE;
-        if (fabs(dE) < 1e-15) break;
-    }
-    return E;
-}
-
+// One thread per anchor.  The per-template constants (Omega, sin and cos w, sqrt(1 - e^2),
+// the zero offset's Delta_R(0)) come with the template from the host, so no thread waits for
+// another; the kernel is bound by the FP64 pipe, so each anchor does one FP64 sincos in the
+// circular case (E = M) and, for e > 0, takes sin E and cos E from the Newton iteration's last
+// evaluation, advanced by its final step dE to first order (the neglected dE^2 / 2 is below
+// 1e-29 once |dE| < 1e-15).
 __global__ void k_anchors(const DevTemplate* __restrict__ bank, int64_t t0, Plan p,
                           Anchor* __restrict__ out)
 {
-    __shared__ double s_delta0;
     const int tl = blockIdx.y;
-    const DevTemplate T = bank[t0 + tl];
-    const double e = T.ecc;
-    double sw, cw;
-    sincos(T.omega, &sw, &cw);
-    const double rt = sqrt(1.0 - e * e);
-    if (threadIdx.x == 0) {
-        // zero offset of Algorithm 1: M = alpha at t = 0
-        const double E0 = kepler64(reduce_2pi(T.phi), e);
-        double s0, c0;
-        sincos(E0, &s0, &c0);
-        s_delta0 = T.tau * ((c0 - e) * sw + rt * s0 * cw);
-    }
-    __syncthreads();
     const int64_t b = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     if (b >= p.nanchor) return;
-    const double Om = kTwoPi / T.porb;
+    const DevTemplate T = bank[t0 + tl];
+    const double e = T.ecc, sw = T.sw, cw = T.cw, rt = T.rt, Om = T.om;
     const int64_t mc = (b << p.logB) + (1ll << (p.logB - 1));
     const double tc = (double)mc * p.tsamp;
     const double M = reduce_2pi(Om * tc + T.phi);
-    const double E = kepler64(M, e);
     double sE, cE;
-    sincos(E, &sE, &cE);
+    if (e == 0.0) {
+        sincos(M, &sE, &cE);  // Kepler's equation gives E = M
+    } else {
+        // Kepler's equation E - e sin E = M by Newton iteration from E0 = M + e sin M,
+        // keeping the last sincos
+        double E = M + e * sin(M), s = 0.0, c = 1.0, dE = 0.0;
+        for (int it = 0; it < 40; ++it) {
+            sincos(E, &s, &c);
+            dE = (E - e * s - M) / (1.0 - e * c);
+            E -= dE;
+            if (fabs(dE) < 1e-15) break;
+        }
+        sE = s - c * dE;
+        cE = c + s * dE;
+    }
     const double Dc = T.tau * ((cE - e) * sw + rt * sE * cw);
-    const double O = (s_delta0 - Dc) / p.tsamp;
+    const double O = (T.delta0 - Dc) * p.inv_tsamp;
     const double If = floor(O);
     const double f = O - If;
-    const double K = T.tau / p.tsamp;
+    const double K = T.tau * p.inv_tsamp;
     const double ws = Om * p.tsamp;
     const double D = 1.0 - e * cE;
-    const double g = ws / D;
+    const double invD = 1.0 / D;
+    const double g = ws * invD;
     const double Ac = cE * sw + rt * sE * cw;   // -(d^2 BT / dE^2) - e sin w
     const double Bc = -sE * sw + rt * cE * cw;  // d BT / dE
     const double L = K * Bc * g;
-    const double u2 = -e * sE * g * g / (2.0 * D);
-    const double u3 = -(e * sE * g * u2 + e * cE * g * g * g / 6.0) / D;
+    const double u2 = -0.5 * e * sE * g * g * invD;
+    const double u3 = -(e * sE * g * u2 + e * cE * g * g * g / 6.0) * invD;
     const double q2 = K * (Bc * u2 - Ac * g * g / 2.0);
     const double q3 = K * (Bc * u3 - Ac * g * u2 - Bc * g * g * g / 6.0);
     Anchor a;
@@ -94,7 +92,7 @@ __global__ void k_anchors(const DevTemplate* __restrict__ bank, int64_t t0, Plan
     a.g = (float)g;
     a.esE = (float)(e * sE);
     a.ecE = (float)(e * cE);
-    a.invD = (float)(1.0 / D);
+    a.invD = (float)invD;
     a.KBc = (float)(K * Bc);
     a.KAc = (float)(K * Ac);
     a.pad0 = a.pad1 = a.pad2 = 0.f;
