@@ -211,15 +211,20 @@ __global__ void __launch_bounds__(256, 4) k_median_warp(float* __restrict__ P, P
 }
 
 // The same from pass 2's row-major power (kLogPowCols: columns in blocks of 8, rows in
-// groups of T = NP = 2^LOGT, W <= R, T <= W): a CTA of kMedCols = 8 warps takes the 8
+// groups of T = NP = 2^LOGT, T <= 2, W <= R): a CTA of kMedCols = 8 warps takes the 8
 // blocks at k2 in [k20, k20 + 8), k1 in [q0, q0 + W) -- one contiguous run of 32 W bytes
-// -- into a shared tile padded to kMedCols + 1 words per row (conflict-free column
-// reads); warp w takes the median of column k20 + w and writes its whitened block to P in
-// bin order.  (Measured at C = 2048 and 4096: 8 columns with four CTAs per SM beat 16 with
-// two, whose 16 warps need more than 64 registers with the candidate gather of the
-// median.)
+// -- into a column-major shared tile (column c = block k20 + c, stride W + 4 words); warp
+// w takes the median of column w (consecutive words: conflict-free) and writes its
+// whitened block to P in bin order.  A float4 of the run holds T rows of 4 / T columns;
+// with T = 2 its elements are two pairs of rows adjacent in the tile, written as two 8-byte
+// stores.  The stride's 4 words of padding spread the stores over all banks (two
+// wavefronts per 8-byte store instruction, one per 4-byte one; a row-major tile padded to
+// 9 words a row had two-way conflicts on every 4-byte store).  (Measured at C = 2048 and
+// 4096: 8 columns with four CTAs per SM beat 16 with two, whose 16 warps need more than 64
+// registers with the candidate gather of the median.)
 constexpr int kMedCols = 8;
 constexpr int kLogMedCols = 3;
+constexpr int kMedPad = 4;
 static_assert(kLogMedCols == kLogPowCols, "the median CTA takes one column block");
 
 template <int VPL, int LOGT>
@@ -227,11 +232,12 @@ __global__ void __launch_bounds__(32 * kMedCols) k_median_warp_t(const float* __
                                                                    float* __restrict__ P,
                                                                    float* __restrict__ scale)
 {
+    static_assert(LOGT == 0 || LOGT == 1, "rows in groups of one or two");
     constexpr int W = 32 * VPL;
-    constexpr int TS = kMedCols + 1;  // tile row stride (words)
-    extern __shared__ uint32_t tsm[];
-    uint32_t* tile = tsm;                  // W x TS
-    uint32_t* hist = tsm + W * TS;         // kMedCols x 288
+    constexpr int CS = W + kMedPad;  // tile column stride (words)
+    extern __shared__ __align__(16) uint32_t tsm[];
+    uint32_t* tile = tsm;                   // kMedCols columns of W words
+    uint32_t* hist = tsm + kMedCols * CS;   // kMedCols x 288
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
     const int tl = blockIdx.y;
     const int lg = p.logC - kLogMedCols;  // groups of kMedCols k2 per row
@@ -242,44 +248,36 @@ __global__ void __launch_bounds__(32 * kMedCols) k_median_warp_t(const float* __
     constexpr int LCH = kLogMedCols + LOGT;  // log2 of the floats of one group's kMedCols columns
     const float* g0 = src + ((int64_t)(k20 >> kLogMedCols) << (p.logR + kLogMedCols)) +
                       ((int64_t)(q0 >> LOGT) << LCH);
-    // thread t loads float4 t + 256 i (i < W / 32): floats f = 4 t + 1024 i.  1024 is a
-    // multiple of the group size 2^LCH, so the place in the group (o) is the same for all
-    // of a thread's loads and the group index steps by 1024 / 2^LCH: each element's tile
-    // slot is the thread's first slot plus a constant per i.
+    // thread t loads float4 t + 256 i: floats f = 4 t + 1024 i, group f / 2^LCH (rows
+    // T (f / 2^LCH) + 0..T-1), place o = f mod 2^LCH in it (element o + u: column (o + u) / T,
+    // row offset (o + u) mod T).  1024 is a whole number of groups, so o is the same for all
+    // of a thread's loads.
     constexpr int FSTEP = 4 * 32 * kMedCols;
     static_assert(FSTEP % (1 << LCH) == 0, "load step is a whole number of groups");
-    if (W * kMedCols >= FSTEP) {
-        const int f0 = 4 * (int)threadIdx.x;
-        const int o = f0 & ((1 << LCH) - 1);
-        uint32_t* trow = tile + ((f0 >> LCH) << LOGT) * TS;
-        int slot[4];
-#pragma unroll
-        for (int u = 0; u < 4; ++u) slot[u] = ((o + u) & ((1 << LOGT) - 1)) * TS + ((o + u) >> LOGT);
+    const int nf4 = (W * kMedCols) / 4;
+    const int f0 = 4 * (int)threadIdx.x;
+    const int o = f0 & ((1 << LCH) - 1);
 #pragma unroll 4
-        for (int i = 0; i < (W * kMedCols) / FSTEP; ++i) {
-            const float4 v = __ldg(reinterpret_cast<const float4*>(g0 + f0 + i * FSTEP));
-            const float e[4] = {v.x, v.y, v.z, v.w};
-            uint32_t* tr = trow + i * ((FSTEP >> LCH) << LOGT) * TS;
-#pragma unroll
-            for (int u = 0; u < 4; ++u) tr[slot[u]] = __float_as_uint(e[u]);
-        }
-    } else {  // W < 128: fewer float4s than threads
-        for (int i = threadIdx.x; i < (W * kMedCols) / 4; i += 32 * kMedCols) {
-            const int f = 4 * i;
-            const int gi = f >> LCH, o = f & ((1 << LCH) - 1);
-            const float4 v = __ldg(reinterpret_cast<const float4*>(g0 + f));
-            const float e[4] = {v.x, v.y, v.z, v.w};
-#pragma unroll
-            for (int u = 0; u < 4; ++u) {
-                const int c = (o + u) >> LOGT, r = (gi << LOGT) + ((o + u) & ((1 << LOGT) - 1));
-                tile[r * TS + c] = __float_as_uint(e[u]);
-            }
+    for (int i = 0; i < (W * kMedCols + FSTEP - 1) / FSTEP; ++i) {
+        if ((int)threadIdx.x + i * 32 * kMedCols >= nf4) break;  // W < 128: fewer float4s than threads
+        const float4 v = __ldg(reinterpret_cast<const float4*>(g0 + f0 + i * FSTEP));
+        const int r0 = ((f0 + i * FSTEP) >> LCH) << LOGT;
+        if (LOGT == 1) {
+            *reinterpret_cast<uint2*>(tile + (o >> 1) * CS + r0) =
+                make_uint2(__float_as_uint(v.x), __float_as_uint(v.y));
+            *reinterpret_cast<uint2*>(tile + ((o >> 1) + 1) * CS + r0) =
+                make_uint2(__float_as_uint(v.z), __float_as_uint(v.w));
+        } else {
+            tile[o * CS + r0] = __float_as_uint(v.x);
+            tile[(o + 1) * CS + r0] = __float_as_uint(v.y);
+            tile[(o + 2) * CS + r0] = __float_as_uint(v.z);
+            tile[(o + 3) * CS + r0] = __float_as_uint(v.w);
         }
     }
     __syncthreads();
     uint32_t u[VPL];
 #pragma unroll
-    for (int i = 0; i < VPL; ++i) u[i] = tile[(lane + 32 * i) * TS + warp];
+    for (int i = 0; i < VPL; ++i) u[i] = tile[warp * CS + lane + 32 * i];
     const float med = __uint_as_float(warp_lower_median<VPL>(u, hist + 288 * warp, lane));
     const float sc = (med > 0.f) ? kLn2 / med : 0.f;
     const int64_t nblk = p.M >> p.logW;
@@ -291,7 +289,7 @@ __global__ void __launch_bounds__(32 * kMedCols) k_median_warp_t(const float* __
 }
 
 template <int VPL>
-constexpr size_t med_t_smem() { return sizeof(uint32_t) * ((size_t)32 * VPL * (kMedCols + 1) + 288 * kMedCols); }
+constexpr size_t med_t_smem() { return sizeof(uint32_t) * ((size_t)kMedCols * (32 * VPL + kMedPad) + 288 * kMedCols); }
 
 
 // Self-test of the bounded waits: an mbarrier expecting one arrival that nothing makes,
