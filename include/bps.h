@@ -92,7 +92,8 @@ typedef struct {
     int32_t batch;         /* templates per launch batch; 0 = library's choice       */
     int32_t log_tile;      /* FFT pass-1 tile: 2^log_tile complex values per CTA,    */
                            /* 13 or 14; 0 = library's choice (14)                     */
-    int32_t log_tile2;     /* FFT pass-2 tile, 13 or 14; 0 = library's choice (13)   */
+    int32_t log_tile2;     /* FFT pass-2 tile, 12, 13 or 14 (at least one row pair); */
+                           /* 0 = library's choice (13)                               */
     int32_t log_cols;      /* log2 C of the four-step split N/2 = R x C (pass-1 column  */
                            /* length R, pass-2 row length C: the radix structure of   */
                            /* both passes), in [max(5, log2(N/2) - 12),               */

@@ -670,6 +670,7 @@ try {
     cudaEventCreate(&e0);
     cudaEventCreate(&e1);
     const int tiles[2] = {13, 14};
+    const int tiles2[3] = {12, 13, 14};  // pass 2 (2^12: four 256-thread CTAs per SM)
     const int batches[4] = {8, 16, 32, 64};
     // four-step splits: the caller's, else the library's and its valid neighbours
     const int logM = ilog2(s->n) - 1;
@@ -692,7 +693,7 @@ try {
     // pass 2: the one-phase kernel at both tiles, and the TMA-fed one (2^13 tiles) where built
     std::vector<std::pair<int, int>> p2;  // (kind, tile)
     if (base->pass2_kind != BPS_PASS2_TMA)
-        for (int t : tiles) p2.push_back({BPS_PASS2_FUSED, t});
+        for (int t : tiles2) p2.push_back({BPS_PASS2_FUSED, t});
     if (base->mode == BPS_MODE_FUSED && base->pass2_kind != BPS_PASS2_FUSED) p2.push_back({BPS_PASS2_TMA, 13});
     for (int lc : splits)
     for (auto k1 : p1)

@@ -55,7 +55,7 @@ struct Plan {
     int logG;       // columns per CTA in pass 1
     int logNP;      // row pairs per CTA in pass 2
     int logTile;    // complex values per CTA tile of pass 1 (13 or 14)
-    int logTile2;   // complex values per CTA tile of pass 2 (13 or 14)
+    int logTile2;   // complex values per CTA tile of pass 2 (12, 13 or 14)
     int logB;       // anchor block length B (samples)
     int64_t nanchor;// N / B
     int logW;       // whitening block W (bins)
@@ -82,8 +82,9 @@ inline bool ws_pass1_built(int logR, int logC)
 }
 
 // Four-step split of the packed FFT, M = R * C, with CTA tiles of 2^logTile (pass 1)
-// and 2^logTile2 (pass 2) complex values in shared memory (13: 256 threads, two CTAs
-// per SM; 14: 512 threads, one): C = 2^min(10, logM - 5) row length (pass 2), raised
+// and 2^logTile2 (pass 2) complex values in shared memory (pass 1 at 32 elements per
+// thread: 2^13 = 256 threads, two CTAs per SM, 2^14 = 512, one; pass 2 at 16: 2^12 = 256
+// threads, four CTAs per SM, 2^13 two, 2^14 one): C = 2^min(10, logM - 5) row length (pass 2), raised
 // to M / 2^12 where R would exceed 2^12 column length (pass 1), unless logCols (checked
 // by log_cols_ok) chooses another split; G = tile1 / R adjacent columns per pass-1 CTA,
 // NP = tile2 / (2C) row pairs per pass-2 CTA.

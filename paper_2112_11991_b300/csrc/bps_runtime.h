@@ -182,8 +182,8 @@ inline int check_params(bps_ctx* ctx, const bps_search_params* pr, int64_t n)
         return fail(ctx, BPS_ERR_INVALID_ARG, "unknown mode %d", pr->mode);
     if (pr->batch < 0) return fail(ctx, BPS_ERR_INVALID_ARG, "batch must be >= 0");
     if ((pr->log_tile != 0 && pr->log_tile != 13 && pr->log_tile != 14) ||
-        (pr->log_tile2 != 0 && pr->log_tile2 != 13 && pr->log_tile2 != 14))
-        return fail(ctx, BPS_ERR_INVALID_ARG, "log_tile and log_tile2 must be 0, 13 or 14");
+        (pr->log_tile2 != 0 && (pr->log_tile2 < 12 || pr->log_tile2 > 14)))
+        return fail(ctx, BPS_ERR_INVALID_ARG, "log_tile must be 0, 13 or 14, log_tile2 0 or 12..14");
     if (pr->log_cols != 0 && !log_cols_ok(ilog2(n) - 1, pr->log_cols))
         return fail(ctx, BPS_ERR_INVALID_ARG, "log_cols %d is not a valid split of %lld samples",
                     pr->log_cols, (long long)n);

@@ -1249,8 +1249,9 @@ __global__ void k_power_r2c(const float2* __restrict__ X, Plan p, float* __restr
 size_t tile_smem(int logt) { return (size_t)(((1 << logt) + ((1 << logt) >> 4) + 64) * sizeof(float2)); }
 
 // Compile-time geometries of the two passes for 2^20..2^25 samples at pass-1 tiles 2^13 /
-// 2^14 and pass-2 tiles 2^13 / 2^14, with the library's four-step split and, for 2^23 and
-// 2^24, the split with twice the row length (other plans use the <-1, -1, -1> kernels).
+// 2^14 and pass-2 tiles 2^12 / 2^13 / 2^14, with the library's four-step split and, for
+// 2^23 and 2^24, the split with twice the row length (other plans use the <-1, -1, -1>
+// kernels).
 using Pass1Fn = void (*)(SeriesView, const Anchor*, Plan, const float2*, float2*);
 using Pass2Fn = void (*)(const float2*, Plan, const float2*, float*);
 
@@ -1260,7 +1261,7 @@ using Pass2Fn = void (*)(const float2*, Plan, const float2*, float*);
     X(12, 11, 1) X(12, 12, 2) X(12, 12, 1) X(11, 11, 3) X(11, 11, 2) X(11, 12, 3) X(11, 12, 2) \
     X(-1, -1, -1)
 #define BPS_PASS2_GEOMETRIES(X) \
-    X(9, 10, 2) X(9, 10, 3) \
+    X(9, 10, 2) X(9, 10, 3) X(9, 10, 1) X(10, 10, 1) X(11, 10, 1) X(12, 10, 1) X(12, 11, 0) X(11, 11, 0) \
     X(10, 10, 2) X(10, 10, 3) X(11, 10, 2) X(11, 10, 3) X(12, 10, 2) X(12, 10, 3) X(12, 11, 1) \
     X(12, 11, 2) X(12, 12, 0) X(12, 12, 1) X(11, 11, 1) X(11, 11, 2) X(11, 12, 0) X(11, 12, 1) \
     X(-1, -1, -1)

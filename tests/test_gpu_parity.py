@@ -287,7 +287,7 @@ def test_autotune_choice_and_invariance(bps, ctx, w1):
     ref, _ = ctx.fetch_candidates(ctx.search(sid, bid, bps.default_params(log_tile=14, log_tile2=13,
                                                                         batch=8)))
     best, ms = ctx.autotune(sid, bid, bps.default_params(), sample_templates=8)
-    assert best.log_tile in (13, 14) and best.log_tile2 in (13, 14) and best.batch in (4, 8)
+    assert best.log_tile in (13, 14) and best.log_tile2 in (12, 13, 14) and best.batch in (4, 8)
     # 2^18 samples: the default split (10) or one the autotuner also tries (-1, +1, +2)
     assert best.log_cols in (9, 10, 11, 12)
     assert ms > 0
@@ -322,6 +322,34 @@ def test_pass1_tiles_identical(bps, ctx, logn):
                    ctx.fetch_candidates(ctx.search(sid, bid, prm))[0])
     assert np.array_equal(res[13][0], res[14][0])
     assert np.array_equal(res[13][1], res[14][1]) and res[13][1].size > 0
+    ctx.unload(sid)
+    ctx.unload(bid)
+
+
+@pytest.mark.parametrize("logn,log_cols", [(16, 0), (19, 0), (21, 0), (23, 11)])
+def test_pass2_tiles_identical(bps, ctx, logn, log_cols):
+    """Pass-2 tiles of 2^12, 2^13 and 2^14 complex (NP = tile / 2C row pairs per CTA, one,
+    two or four CTAs per SM; row-major or bin-order power by NP) compute the same floats:
+    every row FFT, split and power runs the same operations whatever the tile.  2^23 at
+    C = 2048 is the benchmark's split (NP = 1, 2 and 4)."""
+    n, ts = 1 << logn, 64e-6
+    T = n * ts
+    p = synth.Pulsar(period_s=0.023, porb_s=6 * T, tau_lts=0.06, phi_rad=1.4, amp=0.3)
+    x = synth.inject(synth.noise(n, 1100 + logn), ts, p)
+    K = 3 if logn >= 23 else 5
+    bank, _ = synth.uniform_bank(K, 2100 + logn, (3 * T, 10 * T), (0.0, 0.1),
+                                 true_orbits=[p.orbit()])
+    sid = ctx.load_series(x, ts)
+    bid = ctx.load_bank(bank)
+    res = {}
+    for t2 in (12, 13, 14):
+        prm = bps.default_params(log_tile=14, log_tile2=t2, log_cols=log_cols, sigma_thr=5.0)
+        res[t2] = (ctx.whitened_spectrum(sid, bid, 0, K, n, prm),
+                   ctx.fetch_candidates(ctx.search(sid, bid, prm))[0])
+    for t2 in (12, 14):
+        assert np.array_equal(res[13][0].view(np.uint32), res[t2][0].view(np.uint32)), t2
+        assert np.array_equal(res[13][1], res[t2][1]), t2
+    assert res[13][1].size > 0
     ctx.unload(sid)
     ctx.unload(bid)
 
