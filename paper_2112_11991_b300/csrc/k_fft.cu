@@ -508,26 +508,27 @@ __global__ void __launch_bounds__(512, 1) k_pass1(SeriesView x, const Anchor* __
 #pragma unroll
         for (int s = 0; s < 16; ++s) d1[G * s + ((G * s) >> 4)] = v1[Radix<4>::out_pos(s)];
     } else {
+        // one column per butterfly (G = 1: a column fills the tile)
 #pragma unroll 1
-    for (int i = 0; i < BPT1; ++i) {
-        const int b = threadIdx.x + i * nthr;
-        const int g = b & (G - 1);
-        const int j = b >> logG;
-        int id[32];
-        pass1_indices(at, p.logB, logQ, logC, c0 + g, j, id);
-        float2 v[16];
-        if (!F16) {
+        for (int i = 0; i < BPT1; ++i) {
+            const int b = threadIdx.x + i * nthr;
+            const int g = b & (G - 1);
+            const int j = b >> logG;
+            int id[32];
+            pass1_indices(at, p.logB, logQ, logC, c0 + g, j, id);
+            float2 v[16];
+            if (!F16) {
 #pragma unroll
-            for (int s = 0; s < 16; ++s) v[s] = gather_pair_f32(x, n, id[2 * s], id[2 * s + 1]);
-        } else {
-            gather_f16_butterfly(x, n, id, v);
+                for (int s = 0; s < 16; ++s) v[s] = gather_pair_f32(x, n, id[2 * s], id[2 * s + 1]);
+            } else {
+                gather_f16_butterfly(x, n, id, v);
+            }
+            Radix<4>::dft(v);
+            // pad(g + 16 G j + G s) = pad(g + 16 G j) + G s + (G s) / 16, as g < G
+            float2* d = sm + pad(g + 16 * G * j);
+#pragma unroll
+            for (int s = 0; s < 16; ++s) d[G * s + ((G * s) >> 4)] = v[Radix<4>::out_pos(s)];
         }
-        Radix<4>::dft(v);
-        // pad(g + 16 G j + G s) = pad(g + 16 G j) + G s + (G s) / 16, as g < G
-        float2* d = sm + pad(g + 16 * G * j);
-#pragma unroll
-        for (int s = 0; s < 16; ++s) d[G * s + ((G * s) >> 4)] = v[Radix<4>::out_pos(s)];
-    }
     }
     __syncthreads();
     int logNs = 4;
