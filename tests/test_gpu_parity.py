@@ -354,6 +354,34 @@ def test_pass2_tiles_identical(bps, ctx, logn, log_cols):
     ctx.unload(bid)
 
 
+@pytest.mark.parametrize("logn", [17, 23])
+def test_f16_uniform_scale_bit_exact(bps, ctx, logn):
+    """FP16 storage with one power-of-two scale for all blocks (here 2^8: |x| < 4
+    everywhere): the whitened power and the candidates equal, bit for bit, the FP32 path on
+    the series quantised the same way in numpy, half(x / 2^8) * 2^8 (round-to-nearest-even
+    FP16 conversion): the packing rounds like numpy and the FP16 gather dequantises
+    exactly.  tau = 0 templates map every sample inside the series, so the fill value (the
+    mean of the unquantised series for FP16 storage) plays no part."""
+    n, ts = 1 << logn, 64e-6
+    rng = np.random.default_rng(1200 + logn)
+    x = np.clip(rng.standard_normal(n), -3.9, 3.9).astype(np.float32)
+    xq = ((x / np.float32(256.0)).astype(np.float16).astype(np.float32) * np.float32(256.0))
+    T = n * ts
+    bank = np.array([[4.0 * T, 0.0, 0.3, 0.0, 0.0], [7.0 * T, 0.0, 2.1, 0.0, 0.0]])
+    s16 = ctx.load_series(x, ts, bps.BPS_F16_SCALED)
+    sq = ctx.load_series(xq, ts)
+    bid = ctx.load_bank(bank)
+    prm = bps.default_params(sigma_thr=5.0)
+    a = ctx.whitened_spectrum(s16, bid, 0, 2, n, prm)
+    b = ctx.whitened_spectrum(sq, bid, 0, 2, n, prm)
+    assert np.array_equal(a.view(np.uint32), b.view(np.uint32))
+    ca, _ = ctx.fetch_candidates(ctx.search(s16, bid, prm))
+    cb, _ = ctx.fetch_candidates(ctx.search(sq, bid, prm))
+    assert np.array_equal(ca, cb)
+    for i in (s16, sq, bid):
+        ctx.unload(i)
+
+
 def test_bounded_wait_expires_and_context_survives(bps, ctx, w1):
     """A kernel polling an mbarrier whose phase nothing completes gives up after its
     limit and reports it; the context keeps working (a search right after matches one
